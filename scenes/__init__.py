@@ -1,0 +1,193 @@
+"""Seeded synthetic triangle scenes that stand in for the paper's benchmark scenes.
+
+The paper (Sec. 4, Table 1) measures grid construction on non-homogeneous and
+architectural scenes (Fairy Forest, Crytek Sponza, San Miguel, ...).  Those
+meshes are not available, so the workloads below are generated from seeds with
+the same character: uniform soups, soups with a heavy tail of large triangles,
+and an architectural scene of large axis-aligned wall quads plus clustered
+small clutter.
+
+This module only draws inputs.  It holds none of the grid-construction
+arithmetic, and both the CUDA path and the CPU oracle consume what it returns.
+Every generator is deterministic for a given seed (numpy's counter-based Philox
+bit generator) and returns float32 vertices ``[nv, 3]`` and int32 triangles
+``[n, 3]``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED_BASE = 0xC0FFEE
+
+
+@dataclasses.dataclass
+class Scene:
+    name: str
+    verts: np.ndarray  # float32 [nv, 3]
+    tris: np.ndarray   # int32 [n, 3]
+    lam: float         # grid density: target cells per triangle
+
+    @property
+    def n(self) -> int:
+        return int(self.tris.shape[0])
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=int(seed)))
+
+
+def _unit_vectors(g: np.random.Generator, n: int) -> np.ndarray:
+    """Directions uniform on the unit sphere (normalised Gaussians)."""
+    d = g.standard_normal((n, 3))
+    nrm = np.sqrt((d * d).sum(axis=1, keepdims=True))
+    nrm[nrm == 0.0] = 1.0
+    return d / nrm
+
+
+def _soup(c: np.ndarray, e1: np.ndarray, e2: np.ndarray):
+    """Triangle soup with centroid c and edge vectors e1, e2 from v0."""
+    v0 = c - (e1 + e2) / 3.0
+    v1 = v0 + e1
+    v2 = v0 + e2
+    n = c.shape[0]
+    verts = np.empty((n, 3, 3), dtype=np.float32)
+    verts[:, 0] = v0
+    verts[:, 1] = v1
+    verts[:, 2] = v2
+    tris = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    return verts.reshape(3 * n, 3), tris
+
+
+def uniform_soup(n: int = 100_000, seed: int = SEED_BASE + 1, lam: float = 2.0) -> Scene:
+    """Uniform soup: centroids U[0,1]^3, edge vectors U[-0.01,0.01]^3."""
+    g = rng(seed)
+    c = g.random((n, 3))
+    e1 = g.uniform(-0.01, 0.01, (n, 3))
+    e2 = g.uniform(-0.01, 0.01, (n, 3))
+    v, t = _soup(c, e1, e2)
+    return Scene(f"uniform_soup_{n}", v, t, lam)
+
+
+def nonhomogeneous_soup(n: int = 1_000_000, seed: int = SEED_BASE + 2, lam: float = 4.0,
+                        extent: float = 100.0, large_frac: float = 0.01) -> Scene:
+    """Non-homogeneous soup: centroids U[0,extent]^3; 99% small triangles with
+    edge lengths LogNormal(ln 0.05, 0.5), 1% large with lengths U[5,40], all
+    with directions uniform on the sphere.  The large ones are picked by a
+    seeded permutation, so a single triangle can span 1 to ~1e4+ cells."""
+    g = rng(seed)
+    c = g.random((n, 3)) * extent
+    nlarge = int(round(large_frac * n))
+    is_large = np.zeros(n, dtype=bool)
+    is_large[g.permutation(n)[:nlarge]] = True
+    l1 = g.lognormal(math.log(0.05), 0.5, n)
+    l2 = g.lognormal(math.log(0.05), 0.5, n)
+    big1 = g.uniform(5.0, 40.0, n)
+    big2 = g.uniform(5.0, 40.0, n)
+    l1 = np.where(is_large, big1, l1)
+    l2 = np.where(is_large, big2, l2)
+    e1 = _unit_vectors(g, n) * l1[:, None]
+    e2 = _unit_vectors(g, n) * l2[:, None]
+    v, t = _soup(c, e1, e2)
+    return Scene(f"nonhomogeneous_soup_{n}", v, t, lam)
+
+
+def architectural(n: int = 10_000_000, seed: int = SEED_BASE + 3, lam: float = 8.0,
+                  size=(200.0, 50.0, 200.0), nblobs: int = 2000,
+                  quad_frac: float = 0.05) -> Scene:
+    """Architectural-style scene: a ``size`` building of axis-aligned wall and
+    floor quads (side lengths log-uniform in [0.5, 20], clipped to the
+    building, each split into 2 triangles sharing 2 of its 4 vertices: about
+    ``quad_frac`` of the triangles), plus clutter of small randomly oriented
+    triangles (edges log-uniform in [0.01, 0.3]) clustered in ``nblobs``
+    Gaussian blobs of sigma 1.5 whose centres are uniform in the building.
+    The quads form an indexed mesh, so this scene exercises the vertex
+    gather through ``tris``."""
+    g = rng(seed)
+    size = np.asarray(size, dtype=np.float64)
+    nquad = int(round(quad_frac * n / 2))
+    nclut = n - 2 * nquad
+
+    # --- wall / floor quads ---------------------------------------------------
+    axis = g.integers(0, 3, nquad)                     # normal axis
+    lo_side, hi_side = math.log(0.5), math.log(20.0)
+    sa = np.exp(g.uniform(lo_side, hi_side, nquad))
+    sb = np.exp(g.uniform(lo_side, hi_side, nquad))
+    u_ax = (axis + 1) % 3                              # first in-plane axis
+    w_ax = (axis + 2) % 3                              # second in-plane axis
+    sa = np.minimum(sa, size[u_ax])
+    sb = np.minimum(sb, size[w_ax])
+    cu = g.random(nquad) * (size[u_ax] - sa)
+    cw = g.random(nquad) * (size[w_ax] - sb)
+    plane = g.random(nquad) * size[axis]
+    corners = np.zeros((nquad, 4, 3), dtype=np.float64)
+    rows = np.arange(nquad)
+    for k, (du, dw) in enumerate(((0, 0), (1, 0), (1, 1), (0, 1))):
+        corners[rows, k, axis] = plane
+        corners[rows, k, u_ax] = cu + du * sa
+        corners[rows, k, w_ax] = cw + dw * sb
+    qverts = corners.reshape(4 * nquad, 3)
+    base = 4 * np.arange(nquad, dtype=np.int64)
+    qtris = np.empty((nquad, 2, 3), dtype=np.int64)
+    qtris[:, 0] = np.stack([base, base + 1, base + 2], axis=1)
+    qtris[:, 1] = np.stack([base, base + 2, base + 3], axis=1)
+    qtris = qtris.reshape(2 * nquad, 3)
+
+    # --- clutter ----------------------------------------------------------------
+    centres = g.random((nblobs, 3)) * size
+    blob = g.integers(0, nblobs, nclut)
+    c = centres[blob] + g.normal(0.0, 1.5, (nclut, 3))
+    c = np.clip(c, 0.0, size)
+    lo_e, hi_e = math.log(0.01), math.log(0.3)
+    l1 = np.exp(g.uniform(lo_e, hi_e, nclut))
+    l2 = np.exp(g.uniform(lo_e, hi_e, nclut))
+    e1 = _unit_vectors(g, nclut) * l1[:, None]
+    e2 = _unit_vectors(g, nclut) * l2[:, None]
+    cverts, ctris = _soup(c, e1, e2)
+
+    verts = np.concatenate([qverts.astype(np.float32), cverts], axis=0)
+    tris = np.concatenate([qtris, ctris.astype(np.int64) + 4 * nquad], axis=0).astype(np.int32)
+    return Scene(f"architectural_{n}", verts, tris, lam)
+
+
+def batch_sizes(nmeshes: int = 64, seed: int = SEED_BASE + 4, lo: float = 1e3, hi: float = 2e6):
+    """Triangle counts log-uniform in [lo, hi] for a batch of meshes."""
+    g = rng(seed)
+    return np.exp(g.uniform(math.log(lo), math.log(hi), nmeshes)).astype(np.int64)
+
+
+def batched_meshes(nmeshes: int = 64, seed: int = SEED_BASE + 4, lam: float = 4.0,
+                   lo: float = 1e3, hi: float = 2e6, scale: float = 1.0):
+    """Independent non-homogeneous soups of uneven sizes; mesh k has N_k
+    triangles in a box of side 100 * cbrt(N_k / 1e6) so the triangle density
+    matches the 1M-triangle soup.  ``scale`` multiplies every N_k (small
+    variants for tests)."""
+    sizes = batch_sizes(nmeshes, seed, lo, hi)
+    out = []
+    for k, nk in enumerate(sizes):
+        nk = max(1, int(round(nk * scale)))
+        ext = 100.0 * (nk / 1e6) ** (1.0 / 3.0)
+        out.append(nonhomogeneous_soup(nk, seed=seed * 1000 + k, lam=lam, extent=ext))
+    return out
+
+
+def tiny_scene(g: np.random.Generator, n: int, nverts: int | None = None,
+               box: float = 1.0, max_edge: float = 0.5) -> Scene:
+    """A small random indexed mesh for exhaustive checks: ``nverts`` vertices
+    (default 3n) and ``n`` triangles drawing random vertex indices."""
+    if nverts is None:
+        nverts = max(3, 3 * n)
+    centers = g.random((nverts, 3)) * box
+    jitter = (g.random((nverts, 3)) - 0.5) * max_edge
+    verts = (centers + jitter).astype(np.float32)
+    tris = g.integers(0, nverts, (n, 3)).astype(np.int32)
+    return Scene(f"tiny_{n}", verts, tris, float(g.uniform(0.5, 8.0)))
+
+
+CONFIGS = {
+    "uniform_1e5": lambda: uniform_soup(),
+    "nonhomogeneous_1e6": lambda: nonhomogeneous_soup(),
+    "architectural_1e7": lambda: architectural(),
+}

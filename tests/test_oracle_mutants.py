@@ -1,0 +1,59 @@
+"""Plants plausible mistakes in copies of oracle.c (on the CPU) and checks
+that the pins of _pins.py catch every one: a dropped term, a wrong sign, a
+wrong index, a transposed operand, an off-by-one, a lost clamp, ..."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "bounds_min_as_max": ("if (p < lo[a]) lo[a] = p;", "if (p > lo[a]) lo[a] = p;"),
+    "bounds_index_off_by_one": ("(int64_t)vi >= nverts", "(int64_t)vi > nverts"),
+    "plan_floor_not_ceil": ("double r = ceil((double)e[a] * k);", "double r = floor((double)e[a] * k);"),
+    "plan_sqrt_not_cbrt": ("(d == 3) ? cbrt(q)", "(d == 3) ? sqrt(q)"),
+    "plan_scale_inverted": ("scale[a] = (float)res[a] / e[a];", "scale[a] = e[a] / (float)res[a];"),
+    "plan_flat_axis_counted": ("if (n > 0 && e[a] > 0.0f) { ++d;", "if (n > 0) { ++d;"),
+    "cell_sign": ("float t = p - lo;", "float t = p + lo;"),
+    "cell_no_clamp_hi": ("if (f > (float)(res - 1)) return res - 1;", "if (f > (float)res) return res - 1;"),
+    "count_exclusive_hi": ("cnt *= (int64_t)(ch - cl + 1);", "cnt *= (int64_t)(ch - cl) + (ch == cl);"),
+    "box_hi_from_min": ("if (k == 0 || p > bh) bh = p;", "if (k == 0 || p < bh) bh = p;"),
+    "scan_inclusive": ("offsets[i] = s;\n        s += V[i];", "s += V[i];\n        offsets[i] = s;"),
+    "markers_from_zero": ("for (int64_t i = 1; i < n; ++i) O[offsets[i]] = 1;",
+                          "for (int64_t i = 0; i < n; ++i) O[offsets[i]] = 1;"),
+    "segment_no_reset": ("if (j == 0 || O[j] != O[j - 1]) run = 0;", "if (j == 0) run = 0;"),
+    "coords_wrong_divisor": ("int64_t y = (rid - z * mx * my) / mx;", "int64_t y = (rid - z * mx * my) / my;"),
+    "coords_x_y_swapped": ("out[0] = lo[0] + (int32_t)x;\n    out[1] = lo[1] + (int32_t)y;",
+                           "out[0] = lo[0] + (int32_t)y;\n    out[1] = lo[1] + (int32_t)x;"),
+    "linear_wrong_index": ("(int64_t)res[1] * (int64_t)g[2]", "(int64_t)res[0] * (int64_t)g[2]"),
+    "sort_unstable_desc": ("return a->j < b->j ? -1 : (a->j > b->j ? 1 : 0);",
+                           "return a->j > b->j ? -1 : (a->j < b->j ? 1 : 0);"),
+    "ranges_inclusive": ("int64_t v = g[c];\n        G[c] = (int32_t)s;\n        s += v;",
+                         "int64_t v = g[c];\n        s += v;\n        G[c] = (int32_t)s;"),
+    "cell_scale_dropped": ("float u = t * scale;", "float u = t;"),
+    "cell_nan_not_zero": ("if (isnan(u)) return 0;\n    float f = floorf(u);", "float f = ceilf(u) - 1.0f;"),
+    "counting_exclusive_scan_shift": ("cnt[c] = s;\n        G[c] = (int32_t)s;",
+                                      "cnt[c] = s + v - v;\n        G[c] = (int32_t)(s + (c > 0));"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mut = tmp_path / "oracle_mut.c"
+    mut.write_text(src.replace(old, new))
+    lib = oracle.compile_source(str(mut), str(tmp_path / "liboracle_mut.so"))
+    code = ("import sys; sys.path[:0] = [%r, %r]\n"
+            "import oracle; oracle.use_library(%r)\n"
+            "import _pins; f = _pins.run_all(); print(f); sys.exit(1 if f else 0)\n") % (ROOT, HERE, lib)
+    # a mutant may also crash (an out-of-range cell id): that counts as caught
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived every pin:\n{r.stdout}\n{r.stderr}"
