@@ -1,0 +1,303 @@
+#!/usr/bin/env python3
+"""Benchmark of the parallel uniform-grid build (Algorithm 1) on GB300.
+
+Workload: the 10M-triangle architectural-style scene (wall/floor quads plus
+clustered clutter, lambda = 8), generated from a seed on the host and
+resident in HBM before timing.  One step = one whole BuildParallelGrid
+(bounds, CountCells + ExclusiveSum, pair generation, radix sort, ranges)
+through the C ABI.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank builds its own grid (independent problems:
+weak scaling, no collective on the data path); value = pairs of all ranks /
+max time over ranks.  --impl reference times the CPU oracle instead (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs/s"
+WORKLOAD = "architectural_1e7"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--radix-bits", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_from_profiles(kernel: str, nrefs: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to this launch's pair count; None if no summary covers the current kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[kernel]
+        return e["dram_bytes_per_pair"] * nrefs
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
+
+
+def make_scene():
+    import scenes
+    return scenes.CONFIGS[WORKLOAD]()
+
+
+def cpu_oracle_rate(scene, stride: int = 1):
+    """Pairs/s of the CPU oracle (counting placement, single thread) on every
+    stride-th triangle of the scene."""
+    import numpy as np
+    import oracle
+    tris = np.ascontiguousarray(scene.tris[::stride])
+    t0 = time.perf_counter()
+    g = oracle.build_grid(scene.verts, tris, scene.lam, method="counting")
+    dt = time.perf_counter() - t0
+    return g.NO / dt, dt, tris.shape[0], g.NO
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores, as the reference arm."""
+    if rank != 0:
+        return
+    scene = make_scene()
+    stride = 10
+    for _ in range(args.warmup):
+        cpu_oracle_rate(scene, stride)
+    rates, secs, ntri, nrefs = [], [], 0, 0
+    for _ in range(args.steps):
+        r, dt, ntri, nrefs = cpu_oracle_rate(scene, stride)
+        rates.append(r)
+        secs.append(dt)
+    tot = sum(secs)
+    value = nrefs * args.steps / tot
+    sample = f"every {stride}th triangle of {WORKLOAD} ({ntri} triangles, {nrefs} pairs) per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_stride": stride},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import paper_2403_10647_gb300 as pg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    scene = make_scene()
+    ctx = pg.Context(local, radix_bits=args.radix_bits)
+    v = torch.from_numpy(scene.verts).cuda()
+    t = torch.from_numpy(scene.tris).cuda()
+    torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        g = ctx.build(v, t, scene.lam)
+        del g
+    info = ctx.build(v, t, scene.lam).info
+    nrefs = info.nrefs
+
+    # ---- device-resident timing ------------------------------------------------
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            g = ctx.build(v, t, scene.lam)
+            del g
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    stats = ctx.kernel_stats()
+    ctx.profile(False)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = nrefs * args.steps * world / (ms_max / 1e3)
+
+    # ---- end to end through the host-buffer entry point ------------------------------
+    e2e = None
+    if not args.no_e2e:
+        hv = torch.from_numpy(scene.verts).pin_memory()
+        ht = torch.from_numpy(scene.tris).pin_memory()
+        hc = torch.empty(info.ncells + 1, dtype=torch.int32).pin_memory()
+        hr = torch.empty(max(nrefs, 1), dtype=torch.int32).pin_memory()
+        for _ in range(2):
+            ctx.build_host(hv, ht, scene.lam, hc, hr)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.build_host(hv, ht, scene.lam, hc, hr)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        dt_t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
+        dt = float(dt_t.item())
+        e2e = {"value": nrefs * args.steps * world / dt, "unit": METRIC,
+               "h2d_bytes_per_step": int(hv.numel() * 4 + ht.numel() * 4),
+               "d2h_bytes_per_step": int((info.ncells + 1 + nrefs) * 4),
+               "ms_per_step": 1e3 * dt / args.steps}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel -------------------------------------------------
+    peak, peak_kind = peaks()
+    kern = {}
+    for name, s in stats.items():
+        if s["launches"] and s["ms"] > 0:
+            per_ms = s["ms"] / s["launches"]
+            kern[name] = {"launches_per_step": s["launches"] / args.steps, "ms_per_launch": per_ms,
+                          "gbs": s["bytes"] / s["launches"] / (per_ms / 1e3) / 1e9,
+                          "bytes_per_launch": s["bytes"] / s["launches"],
+                          "share": s["ms"] / sum(x["ms"] for x in stats.values())}
+    dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches_per_step"])
+    tot_bytes = sum(s["bytes"] for s in stats.values())
+    tot_ms = sum(s["ms"] for s in stats.values())
+    traffic = traffic_from_profiles(dom, nrefs)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kern[dom]["gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "bytes_per_launch": kern[dom]["bytes_per_launch"],
+            "all_kernels_gbs": tot_bytes / (tot_ms / 1e3) / 1e9,
+            "all_kernels_frac": tot_bytes / (tot_ms / 1e3) / 1e9 / peak}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, dt, ntri, nr = cpu_oracle_rate(scene, 1)
+        cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"whole {WORKLOAD} ({ntri} triangles, {nr} pairs), counting placement, "
+                         f"single-threaded C, {dt:.1f} s"}
+
+    launches = int(sum(s["launches"] for s in stats.values()))
+    out = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_tris": scene.n, "lambda": scene.lam, "grid": list(info.res),
+                   "ncells": info.ncells, "nrefs": nrefs, "key_bits": info.key_bits,
+                   "radix_bits": args.radix_bits or 8, "l2": "inputs larger than L2 (474 MB)",
+                   "parallelism": f"replicas{world}"},
+        "builds_per_s": world * args.steps / (ms_max / 1e3),
+        "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    print(json.dumps(out))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

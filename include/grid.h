@@ -1,0 +1,203 @@
+/*
+ * grid.h - C ABI of the GB300 (sm_103a) parallel uniform-grid builder.
+ *
+ * The library builds the compact uniform grid (G, O) of a triangle mesh with
+ * the parallel construction of Costa, Pereira and Jorge, "Building An
+ * Efficient Grid On GPU" (Algorithm 1, Sec. 3):
+ *
+ *   boxes -> CountCells -> ExclusiveSum -> MakeObjectIds -> InclusiveSum ->
+ *   SegmentedExclusiveSum -> MakeCellIds (GlobalCoords) -> RadixSort(C, O) ->
+ *   RunLengthEncode / NonEmptyCells / ExclusiveSum -> (G, O)
+ *
+ * Every step runs in the library's own CUDA kernels.  Signatures use plain
+ * pointers and sizes only.  Unless stated otherwise pointers are DEVICE
+ * pointers on the context's device, read or written in stream order on the
+ * context's current stream (grid_ctx_set_stream); the call returns after the
+ * work is enqueued, except where a host value must be produced (documented
+ * per call), in which case it synchronises that stream.
+ *
+ * Output format (Sec. 3, Fig. 4d, "compact format"):
+ *   cells  int32 [ncells + 1]: cell c's object ids are refs[cells[c] ..
+ *          cells[c + 1]); cells[ncells] == nrefs.  Cell id of grid coordinate
+ *          (x, y, z) is x + res_x * (y + res_y * z).
+ *   refs   int32 [nrefs]: object (triangle) ids in cell order, ascending
+ *          inside each cell.
+ *
+ * World-to-grid mapping (the paper gives the data flow, not the arithmetic;
+ * this is the library's fixed reading):
+ *   res_a   = clamp(ceil(e_a * k), 1, GRID_RES_MAX) with e_a = hi_a - lo_a
+ *             (FP32), k = (lambda * n / prod_nonzero e)^(1/d) in FP64 over the
+ *             d axes of non-zero extent; a zero-extent axis gets res 1.
+ *   scale_a = (float)res_a / e_a (FP32, round to nearest), 0 on a flat axis.
+ *   cell_a(p) = clamp(floor((p - lo_a) * scale_a), 0, res_a - 1) with the
+ *             subtraction and the product each rounded to FP32 (no FMA);
+ *             NaN maps to 0.
+ *   An object's box in grid coordinates is [cell(min vertex), cell(max
+ *   vertex)] per axis, inclusive (GlobalCoords, Sec. 3).
+ *
+ * Error codes: every int-returning call returns GRID_OK (0) or a negative
+ * code below; no call aborts the process.
+ */
+#ifndef GB300_GRID_H
+#define GB300_GRID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRID_OK 0
+#define GRID_EINVAL (-1)     /* bad argument, vertex index out of range, non-finite coordinate */
+#define GRID_ENOMEM (-2)     /* device or host allocation failed */
+#define GRID_EOVERFLOW (-3)  /* ncells or nrefs above INT32_MAX */
+#define GRID_EAGAIN (-4)     /* serving: admission refused, retry later */
+#define GRID_ETIMEOUT (-5)   /* a bounded device wait or a host wait ran out */
+#define GRID_ECUDA (-6)      /* a CUDA runtime call failed */
+#define GRID_ENOSPC (-7)     /* caller's host buffer too small; info holds the sizes */
+#define GRID_ENOTREADY (-8)  /* serving: result not finished yet */
+
+#define GRID_RES_MAX 65535
+
+typedef struct grid_ctx grid_ctx;
+
+/* Grid metadata M plus the build's sizes. */
+typedef struct {
+    float lo[3];          /* scene bounds: union of the triangle boxes */
+    float hi[3];
+    float scale[3];       /* res / extent per axis (0 on a flat axis) */
+    int32_t res[3];       /* cells per axis */
+    int32_t key_bits;     /* bits of the largest cell id: ceil(log2(ncells)) */
+    int64_t ncells;       /* res_x * res_y * res_z */
+    int64_t nrefs;        /* NO: number of <object, cell> pairs */
+    int64_t n;            /* number of objects (triangles) */
+} grid_info;
+
+/* Library-allocated device memory.  Release with grid_buf_free. */
+typedef struct {
+    void *ptr;            /* device pointer, 256-byte aligned; NULL when count == 0 */
+    int64_t count;        /* elements (int32) */
+    size_t bytes;
+} grid_buf;
+
+/* One object's box in grid coordinates plus its pair offset: the per-object
+ * record CountCells + ExclusiveSum produce (16 bytes, 16-byte aligned). */
+typedef struct {
+    uint16_t lo[3];       /* first covered cell per axis */
+    uint16_t hi[3];       /* last covered cell per axis (inclusive) */
+    uint32_t start;       /* exclusive prefix sum of the cell counts V */
+} grid_objrec;
+
+/* Tuning knobs; zero means "library default / autotuned". */
+typedef struct {
+    int32_t radix_bits;   /* widest digit of the LSD radix sort: 8..11 */
+    int32_t reserved[7];
+} grid_opts;
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`: a stream-ordered memory pool,
+ * a control block and the kernels' scratch.  opts may be NULL. */
+int grid_ctx_create(int device, const grid_opts *opts, grid_ctx **out);
+void grid_ctx_destroy(grid_ctx *ctx);
+/* Binds a cudaStream_t (passed as void*; NULL = the context's own stream). */
+int grid_ctx_set_stream(grid_ctx *ctx, void *stream);
+/* Device bytes currently held by the context's pool for outputs + scratch. */
+int grid_ctx_mem_in_use(grid_ctx *ctx, int64_t *bytes);
+const char *grid_strerror(int code);
+/* Library version string. */
+const char *grid_version(void);
+
+/* Per-kernel accounting.  With profiling on, the library brackets each of its
+ * kernel launches with a pair of CUDA events on the launching stream and
+ * records the kernel's algorithmic bytes (the bytes the step must move:
+ * inputs read once, outputs written once).  Launches are counted always. */
+typedef struct {
+    char name[32];        /* kernel family: bounds, count_scan, tile_search, emit, hist, pass_gen, pass, extract */
+    int64_t launches;
+    double total_ms;      /* sum of event-timed durations (0 when profiling is off) */
+    double bytes;         /* sum of algorithmic bytes */
+} grid_kernel_stat;
+
+/* Turns event timing on (1) or off (0) and clears the statistics. */
+int grid_ctx_profile(grid_ctx *ctx, int enable);
+/* Synchronises the stream, resolves pending events and copies up to max
+ * entries (one per kernel family that launched) into out; *count gets the
+ * number written. */
+int grid_ctx_kernel_stats(grid_ctx *ctx, grid_kernel_stat *out, int max, int *count);
+
+/* ---- whole build (Algorithm 1) ------------------------------------------- */
+
+/* BuildParallelGrid (Algorithm 1, Sec. 3) of the triangles tris[n][3]
+ * (int32 vertex indices into verts[nverts][3], float32 xyz) at density
+ * lambda (> 0, finite).  Outputs are allocated from the context's pool:
+ * out_cells (int32 [ncells + 1]) and out_refs (int32 [nrefs]); info may be
+ * NULL.  Synchronises the stream twice (scene bounds, then NO) to size the
+ * outputs; the rest stays on the device.  n == 0 gives res (1,1,1),
+ * cells = [0, 0], refs empty.  Errors: GRID_EINVAL (bad index, non-finite
+ * coordinate, bad lambda, NULL pointer), GRID_EOVERFLOW, GRID_ENOMEM,
+ * GRID_ETIMEOUT, GRID_ECUDA; outputs are left empty on error. */
+int grid_build(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t *tris,
+               int64_t n, float lambda, grid_buf *out_cells, grid_buf *out_refs,
+               grid_info *info);
+
+/* The same build from and to HOST memory: copies the inputs to the device,
+ * builds, copies cells (int32 [ncells + 1]) and refs (int32 [nrefs]) back
+ * into caller buffers of cells_cap / refs_cap elements.  If either is too
+ * small the call returns GRID_ENOSPC with info holding the needed sizes.
+ * Pinned host memory gives asynchronous copies; pageable memory works too.
+ * Returns after the results are in host memory. */
+int grid_build_host(grid_ctx *ctx, const float *h_verts, int64_t nverts, const int32_t *h_tris,
+                    int64_t n, float lambda, int32_t *h_cells, int64_t cells_cap,
+                    int32_t *h_refs, int64_t refs_cap, grid_info *info);
+
+void grid_buf_free(grid_ctx *ctx, grid_buf *buf);
+
+/* ---- the steps one by one (device pointers, caller-allocated outputs) ----- */
+
+/* a0, "boxes" of Algorithm 1: union of the per-triangle boxes, written to host
+ * lo[3], hi[3].  Checks every index and coordinate (GRID_EINVAL).
+ * Synchronises the stream. */
+int grid_bounds(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t *tris,
+                int64_t n, float lo[3], float hi[3]);
+
+/* a1, grid metadata M (host only): resolution, scale and ncells from the
+ * bounds and the density rule above; fills info (nrefs = 0, n set).
+ * GRID_EINVAL for lambda <= 0 or non-finite, GRID_EOVERFLOW if
+ * ncells > INT32_MAX. */
+int grid_plan(const float lo[3], const float hi[3], int64_t n, float lambda, grid_info *info);
+
+/* a2 + a3, CountCells and ExclusiveSum (Algorithm 1, Sec. 3): recs[n] gets
+ * each triangle's box in grid coordinates and the exclusive prefix sum of
+ * the cell counts V; *nrefs = NO = sum of V (host value; synchronises).
+ * info must come from grid_plan for the same triangles.  GRID_EINVAL if a
+ * vertex index is outside [0, nverts) (no vertex is read out of range),
+ * GRID_EOVERFLOW if NO > INT32_MAX. */
+int grid_count_scan(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
+                    const grid_info *info, grid_objrec *recs, int64_t *nrefs);
+
+/* a4 - a7, MakeObjectIds + InclusiveSum + SegmentedExclusiveSum + MakeCellIds
+ * (Algorithm 1, GlobalCoords, Fig. 4a/4b): one thread per pair writes the
+ * object-order lists C (cell id) and O (object id), int32 [nrefs] each. */
+int grid_emit_pairs(grid_ctx *ctx, const grid_objrec *recs, int64_t n, int64_t nrefs,
+                    const grid_info *info, int32_t *C, int32_t *O);
+
+/* a8, RadixSort(C, O) (Algorithm 1, Fig. 4c): stable LSD sort of the pairs by
+ * the low key_bits bits of C (0..31; keys must be < 2^key_bits).  Writes
+ * C_out, O_out (int32 [count]); the inputs are not modified.  The outputs
+ * must not alias the inputs. */
+int grid_sort_pairs(grid_ctx *ctx, const int32_t *C, const int32_t *O, int64_t count,
+                    int32_t key_bits, int32_t *C_out, int32_t *O_out);
+
+/* a9, RunLengthEncode + NonEmptyCells + ExclusiveSum (Algorithm 1, Fig. 4d):
+ * from the cell-sorted C (int32 [count], values in [0, ncells)) writes
+ * cells (int32 [ncells + 1]), cells[c] = number of entries < c. */
+int grid_extract_ranges(grid_ctx *ctx, const int32_t *C_sorted, int64_t count, int64_t ncells,
+                        int32_t *cells);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_GRID_H */

@@ -1,0 +1,239 @@
+"""GB300-native parallel uniform-grid construction (Costa, Pereira, Jorge,
+"Building An Efficient Grid On GPU", Algorithm 1).
+
+A thin Python binding over the C ABI of ``include/grid.h``: every step of the
+build runs in the library's CUDA kernels; this module only passes pointers,
+sizes and the current CUDA stream.  PyTorch supplies device memory and streams.
+Importing the package does not load the library; the first call does, and it
+raises if the library has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+from . import _lib
+from ._lib import GridError, GridInfo, GridBuf, GridOpts, check
+
+__all__ = ["Context", "Info", "Grid", "plan", "GridError"]
+
+
+@dataclasses.dataclass
+class Info:
+    lo: tuple
+    hi: tuple
+    scale: tuple
+    res: tuple
+    key_bits: int
+    ncells: int
+    nrefs: int
+    n: int
+
+    @classmethod
+    def from_c(cls, i: GridInfo) -> "Info":
+        return cls(tuple(i.lo), tuple(i.hi), tuple(i.scale), tuple(i.res), int(i.key_bits),
+                   int(i.ncells), int(i.nrefs), int(i.n))
+
+    def to_c(self) -> GridInfo:
+        c = GridInfo()
+        for a in range(3):
+            c.lo[a], c.hi[a], c.scale[a], c.res[a] = self.lo[a], self.hi[a], self.scale[a], self.res[a]
+        c.key_bits, c.ncells, c.nrefs, c.n = self.key_bits, self.ncells, self.nrefs, self.n
+        return c
+
+
+@dataclasses.dataclass
+class Grid:
+    cells: "object"   # torch int32 [ncells + 1], CUDA
+    refs: "object"    # torch int32 [nrefs], CUDA
+    info: Info
+
+
+def plan(lo, hi, n: int, lam: float) -> Info:
+    """Grid metadata M (resolution, scale, ncells) from scene bounds (host only)."""
+    lib = _lib.load()
+    clo = (ctypes.c_float * 3)(*[float(x) for x in lo])
+    chi = (ctypes.c_float * 3)(*[float(x) for x in hi])
+    info = GridInfo()
+    check(lib.grid_plan(clo, chi, int(n), float(lam), ctypes.byref(info)), "grid_plan")
+    return Info.from_c(info)
+
+
+class _LibBuffer:
+    """Owns one library-allocated device buffer; exposed to torch through the
+    CUDA array interface and released with grid_buf_free when torch drops it."""
+
+    def __init__(self, ctx: "Context", buf: GridBuf):
+        self._ctx = ctx
+        self._buf = buf
+        self.__cuda_array_interface__ = {
+            "shape": (int(buf.count),), "typestr": "<i4", "data": (int(buf.ptr), False),
+            "version": 3, "strides": None, "stream": None,
+        }
+
+    def __del__(self):
+        try:
+            if self._buf.ptr:
+                _lib.load().grid_buf_free(self._ctx._h, ctypes.byref(self._buf))
+        except Exception:
+            pass
+
+
+class Context:
+    """A grid-builder context on one CUDA device (C: grid_ctx)."""
+
+    def __init__(self, device: int = 0, radix_bits: int = 0):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", device)
+        self._lib = _lib.load()
+        opts = GridOpts()
+        opts.radix_bits = int(radix_bits)
+        h = ctypes.c_void_p()
+        check(self._lib.grid_ctx_create(int(device), ctypes.byref(opts), ctypes.byref(h)), "grid_ctx_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.grid_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers -------------------------------------------------------------
+    def _bind_stream(self):
+        s = self._torch.cuda.current_stream(self.device)
+        check(self._lib.grid_ctx_set_stream(self._h, ctypes.c_void_p(s.cuda_stream)), "grid_ctx_set_stream")
+
+    def _dev(self, t, dtype, cols=None):
+        torch = self._torch
+        if not (isinstance(t, torch.Tensor) and t.device == self.device and t.dtype == dtype
+                and t.is_contiguous()):
+            t = torch.as_tensor(t).to(device=self.device, dtype=dtype).contiguous()
+        if cols is not None:
+            t = t.reshape(-1, cols)
+        return t
+
+    def _wrap(self, buf: GridBuf):
+        torch = self._torch
+        if not buf.ptr:
+            return torch.zeros(int(buf.count), dtype=torch.int32, device=self.device)
+        return torch.as_tensor(_LibBuffer(self, buf), device=self.device)
+
+    def profile(self, enable: bool = True) -> None:
+        """Per-kernel CUDA-event timing on (clears the statistics)."""
+        check(self._lib.grid_ctx_profile(self._h, 1 if enable else 0), "grid_ctx_profile")
+
+    def kernel_stats(self) -> dict:
+        """{kernel family: {"launches", "ms", "bytes"}} since the last profile() call."""
+        arr = (_lib.GridKernelStat * 16)()
+        n = ctypes.c_int()
+        check(self._lib.grid_ctx_kernel_stats(self._h, arr, 16, ctypes.byref(n)), "grid_ctx_kernel_stats")
+        return {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].total_ms),
+                                       "bytes": float(arr[i].bytes)} for i in range(n.value)}
+
+    def mem_in_use(self) -> int:
+        v = ctypes.c_int64()
+        check(self._lib.grid_ctx_mem_in_use(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    # -- whole build -----------------------------------------------------------
+    def build(self, verts, tris, lam: float) -> Grid:
+        """BuildParallelGrid on device tensors: verts float32 [nv, 3], tris int32 [n, 3]."""
+        torch = self._torch
+        v = self._dev(verts, torch.float32, 3)
+        t = self._dev(tris, torch.int32, 3)
+        self._bind_stream()
+        cb, rb, info = GridBuf(), GridBuf(), GridInfo()
+        check(self._lib.grid_build(self._h, v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], float(lam),
+                                   ctypes.byref(cb), ctypes.byref(rb), ctypes.byref(info)), "grid_build")
+        return Grid(self._wrap(cb), self._wrap(rb), Info.from_c(info))
+
+    def build_host(self, verts, tris, lam: float, cells_out=None, refs_out=None):
+        """The same build from/to host memory (numpy arrays or CPU tensors,
+        pinned for asynchronous copies).  Returns (cells, refs, info); the
+        output buffers are (re)allocated when missing or too small."""
+        torch = self._torch
+        v = torch.as_tensor(verts).reshape(-1, 3)
+        t = torch.as_tensor(tris).reshape(-1, 3)
+        assert v.dtype == torch.float32 and t.dtype == torch.int32 and v.device.type == "cpu"
+        v, t = v.contiguous(), t.contiguous()
+        info = GridInfo()
+        self._bind_stream()
+
+        def call(co, ro):
+            cp = co.data_ptr() if co is not None else None
+            rp = ro.data_ptr() if ro is not None else None
+            return self._lib.grid_build_host(self._h, v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0],
+                                             float(lam), cp, co.numel() if co is not None else 0, rp,
+                                             ro.numel() if ro is not None else 0, ctypes.byref(info))
+
+        rc = call(cells_out, refs_out)
+        if rc == _lib.GRID_ENOSPC:
+            cells_out = torch.empty(int(info.ncells) + 1, dtype=torch.int32)
+            refs_out = torch.empty(max(int(info.nrefs), 1), dtype=torch.int32)
+            rc = call(cells_out, refs_out)
+        check(rc, "grid_build_host")
+        nc, nr = int(info.ncells) + 1, int(info.nrefs)
+        return cells_out[:nc], refs_out[:nr], Info.from_c(info)
+
+    # -- steps -------------------------------------------------------------------
+    def bounds(self, verts, tris):
+        torch = self._torch
+        v = self._dev(verts, torch.float32, 3)
+        t = self._dev(tris, torch.int32, 3)
+        self._bind_stream()
+        lo, hi = (ctypes.c_float * 3)(), (ctypes.c_float * 3)()
+        check(self._lib.grid_bounds(self._h, v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], lo, hi),
+              "grid_bounds")
+        return tuple(lo), tuple(hi)
+
+    def count_scan(self, verts, tris, info: Info):
+        """CountCells + ExclusiveSum -> (recs int32 [n, 4] (grid_objrec), nrefs)."""
+        torch = self._torch
+        v = self._dev(verts, torch.float32, 3)
+        t = self._dev(tris, torch.int32, 3)
+        recs = torch.empty((t.shape[0], 4), dtype=torch.int32, device=self.device)
+        self._bind_stream()
+        nr = ctypes.c_int64()
+        ci = info.to_c()
+        check(self._lib.grid_count_scan(self._h, v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0],
+                                        ctypes.byref(ci), recs.data_ptr(), ctypes.byref(nr)), "grid_count_scan")
+        return recs, int(nr.value)
+
+    def emit_pairs(self, recs, nrefs: int, info: Info):
+        """MakeObjectIds .. MakeCellIds -> object-order (C, O)."""
+        torch = self._torch
+        C = torch.empty(nrefs, dtype=torch.int32, device=self.device)
+        O = torch.empty(nrefs, dtype=torch.int32, device=self.device)
+        self._bind_stream()
+        ci = info.to_c()
+        check(self._lib.grid_emit_pairs(self._h, recs.data_ptr(), recs.shape[0], int(nrefs), ctypes.byref(ci),
+                                        C.data_ptr(), O.data_ptr()), "grid_emit_pairs")
+        return C, O
+
+    def sort_pairs(self, C, O, key_bits: int):
+        """RadixSort(C, O): stable sort by the low key_bits bits of C."""
+        torch = self._torch
+        C = self._dev(C, torch.int32)
+        O = self._dev(O, torch.int32)
+        Co = torch.empty_like(C)
+        Oo = torch.empty_like(O)
+        self._bind_stream()
+        check(self._lib.grid_sort_pairs(self._h, C.data_ptr(), O.data_ptr(), C.numel(), int(key_bits),
+                                        Co.data_ptr(), Oo.data_ptr()), "grid_sort_pairs")
+        return Co, Oo
+
+    def extract_ranges(self, C_sorted, ncells: int):
+        """RunLengthEncode + NonEmptyCells + ExclusiveSum -> cells [ncells + 1]."""
+        torch = self._torch
+        C = self._dev(C_sorted, torch.int32)
+        G = torch.empty(int(ncells) + 1, dtype=torch.int32, device=self.device)
+        self._bind_stream()
+        check(self._lib.grid_extract_ranges(self._h, C.data_ptr(), C.numel(), int(ncells), G.data_ptr()),
+              "grid_extract_ranges")
+        return G

@@ -1,0 +1,96 @@
+// Launch interface between the host runtime and the grid kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace gg {
+
+// Tile shapes.  COUNT: objects per count/scan tile.  PAIR: pairs per tile of
+// the pair-generation, histogram and radix-sort-pass kernels.  EXTRACT:
+// merged (key, cell) items per range-extraction block.
+constexpr int COUNT_BLOCK = 256;
+constexpr int COUNT_TILE = 2048;
+constexpr int PAIR_BLOCK = 256;
+constexpr int PAIR_TILE = 4096;
+constexpr int EXTRACT_BLOCK = 256;
+constexpr int EXTRACT_TILE = 2048;
+
+enum { SRC_MEM = 0, SRC_GEN = 1 };
+
+struct CountArgs {
+    const float *verts;
+    long long nverts;
+    const int *tris;
+    long long n;
+    float lo[3];
+    float scale[3];
+    int res[3];
+    ObjRec *recs;                   // [n] out
+    unsigned long long *status;     // [ceil(n / COUNT_TILE)] look-back words, zeroed
+    Ctl *ctl;
+};
+
+struct EmitArgs {
+    const ObjRec *recs;
+    const unsigned *tile_obj;       // [ntiles + 1]
+    unsigned res_x, res_y;
+    unsigned count;                 // NO
+    unsigned *C;
+    unsigned *O;
+};
+
+struct HistArgs {
+    const unsigned *keys_in;        // SRC_MEM
+    const ObjRec *recs;             // SRC_GEN
+    const unsigned *tile_obj;       // SRC_GEN
+    unsigned res_x, res_y;          // SRC_GEN
+    unsigned count;
+    unsigned ntiles;
+    int npasses;
+    int shift[MAX_PASSES];
+    int bits[MAX_PASSES];
+    unsigned *hist;                 // [MAX_PASSES][MAX_RADIX], zero on entry, zero on exit
+    unsigned *dbase;                // [MAX_PASSES][MAX_RADIX] out: exclusive digit starts
+    unsigned *status0;              // [ntiles][status_row] zeroed here for the first pass
+    int status_row;
+    Ctl *ctl;
+};
+
+struct PassArgs {
+    const unsigned *keys_in;        // SRC_MEM
+    const unsigned *vals_in;        // SRC_MEM
+    const ObjRec *recs;             // SRC_GEN
+    const unsigned *tile_obj;       // SRC_GEN
+    unsigned res_x, res_y;          // SRC_GEN
+    unsigned *keys_out;
+    unsigned *vals_out;
+    unsigned count;
+    int shift, bits;
+    const unsigned *dbase;          // [2^bits] global digit starts of this pass
+    unsigned *status;               // [ntiles][2^RBITS] zero on entry
+    unsigned *status_next;          // zeroed here for the next pass (nullable)
+    unsigned *ticket;               // zero on entry
+    Ctl *ctl;
+};
+
+struct ExtractArgs {
+    const unsigned *keys;           // sorted
+    unsigned long long count;
+    unsigned long long ncells;
+    unsigned *G;                    // [ncells + 1]
+    Ctl *ctl;
+};
+
+cudaError_t launch_bounds(const float *verts, long long nverts, const int *tris, long long n, Ctl *ctl,
+                          int nsm, cudaStream_t s);
+cudaError_t launch_count_scan(const CountArgs &a, cudaStream_t s);
+cudaError_t launch_tile_search(const ObjRec *recs, long long n, unsigned tile, unsigned ntiles,
+                               unsigned *tile_obj, cudaStream_t s);
+cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s);
+cudaError_t launch_hist(const HistArgs &a, int rbits, int src, int nsm, cudaStream_t s);
+cudaError_t launch_pass(const PassArgs &a, int rbits, int src, unsigned ntiles, cudaStream_t s);
+cudaError_t launch_extract(const ExtractArgs &a, cudaStream_t s);
+
+}  // namespace gg

@@ -1,0 +1,868 @@
+// Host runtime of the grid builder: context, stream-ordered memory pool,
+// grid planner (metadata M of Algorithm 1), build orchestration and the
+// C ABI declared in include/grid.h.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "grid.h"
+#include "kernels.h"
+
+using gg::Ctl;
+using gg::ObjRec;
+
+namespace {
+
+constexpr int64_t kInt32Max = 0x7FFFFFFFll;
+
+// Keeps the caller's current device and restores it on exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Grow-only device buffer from the context's pool.
+struct Scratch {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+enum KernelId { K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_HIST, K_PASS_GEN, K_PASS, K_EXTRACT, K_NUM };
+const char *const kKernelNames[K_NUM] = {"bounds", "count_scan", "tile_search", "emit",
+                                         "hist", "pass_gen", "pass", "extract"};
+
+struct PendingTiming {
+    int kid;
+    cudaEvent_t start, stop;
+};
+
+}  // namespace
+
+struct grid_ctx {
+    int device = 0;
+    int nsm = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;
+    grid_opts opts{};
+    int rbits_max = 8;
+
+    Ctl *d_ctl = nullptr;        // device control block
+    Ctl *h_ctl = nullptr;        // pinned host mirror
+    unsigned *d_hist = nullptr;  // [MAX_PASSES][MAX_RADIX], kept zero between uses
+    unsigned *d_dbase = nullptr; // [MAX_PASSES][MAX_RADIX]
+
+    Scratch recs, k2status, tile_obj, keys[2], vals[2], status[2];
+    Scratch in_verts, in_tris, out_cells, out_refs;  // host-buffer builds
+    std::atomic<int64_t> in_use{0};
+
+    // per-kernel accounting
+    bool profile = false;
+    int64_t launches[K_NUM] = {};
+    double kernel_ms[K_NUM] = {};
+    double kernel_bytes[K_NUM] = {};
+    std::vector<PendingTiming> pending;
+    std::vector<cudaEvent_t> free_events;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e)
+{
+    if (e == cudaSuccess) return GRID_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // not sticky: clear it
+        return GRID_ENOMEM;
+    }
+    return GRID_ECUDA;
+}
+
+#define GG_TRY(expr)                       \
+    do {                                   \
+        int _rc = (expr);                  \
+        if (_rc != GRID_OK) return _rc;    \
+    } while (0)
+
+#define GG_CUDA(expr) GG_TRY(cuda_err(expr))
+
+int pool_alloc(grid_ctx *c, size_t bytes, void **out)
+{
+    *out = nullptr;
+    if (bytes == 0) return GRID_OK;
+    cudaError_t e = cudaMallocFromPoolAsync(out, bytes, c->pool, c->stream);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return cuda_err(e);
+    }
+    c->in_use += (int64_t)bytes;
+    return GRID_OK;
+}
+
+void pool_free(grid_ctx *c, void *p, size_t bytes)
+{
+    if (!p) return;
+    cudaFreeAsync(p, c->stream);
+    c->in_use -= (int64_t)bytes;
+}
+
+int ensure(grid_ctx *c, Scratch &s, size_t bytes)
+{
+    if (s.bytes >= bytes) return GRID_OK;
+    pool_free(c, s.ptr, s.bytes);
+    s.ptr = nullptr;
+    s.bytes = 0;
+    size_t want = bytes + bytes / 8;  // headroom against small growth
+    want = (want + 255) & ~size_t(255);
+    void *p = nullptr;
+    GG_TRY(pool_alloc(c, want, &p));
+    s.ptr = p;
+    s.bytes = want;
+    return GRID_OK;
+}
+
+void release(grid_ctx *c, Scratch &s)
+{
+    pool_free(c, s.ptr, s.bytes);
+    s.ptr = nullptr;
+    s.bytes = 0;
+}
+
+cudaEvent_t take_event(grid_ctx *c)
+{
+    if (!c->free_events.empty()) {
+        cudaEvent_t e = c->free_events.back();
+        c->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets one kernel launch: counts it, adds its algorithmic bytes and, when
+// profiling, records events on the launching stream around it.
+struct KernelScope {
+    grid_ctx *c;
+    int kid;
+    cudaEvent_t start = nullptr;
+    KernelScope(grid_ctx *ctx, int k, double bytes) : c(ctx), kid(k)
+    {
+        c->launches[kid] += 1;
+        c->kernel_bytes[kid] += bytes;
+        if (c->profile) {
+            start = take_event(c);
+            if (start) cudaEventRecord(start, c->stream);
+        }
+    }
+    ~KernelScope()
+    {
+        if (!start) return;
+        cudaEvent_t stop = take_event(c);
+        if (!stop) {
+            c->free_events.push_back(start);
+            return;
+        }
+        cudaEventRecord(stop, c->stream);
+        c->pending.push_back(PendingTiming{kid, start, stop});
+    }
+};
+
+void resolve_timings(grid_ctx *c)
+{
+    for (const PendingTiming &t : c->pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) c->kernel_ms[t.kid] += ms;
+        else cudaGetLastError();
+        c->free_events.push_back(t.start);
+        c->free_events.push_back(t.stop);
+    }
+    c->pending.clear();
+}
+
+// Error bits raised by the kernels -> GRID_* code.
+int ctl_error(unsigned err)
+{
+    if (err & (gg::ERR_BADINDEX | gg::ERR_NONFINITE | gg::ERR_RANGE)) return GRID_EINVAL;
+    if (err & gg::ERR_OVERFLOW) return GRID_EOVERFLOW;
+    if (err & gg::ERR_TIMEOUT) return GRID_ETIMEOUT;
+    return GRID_OK;
+}
+
+int read_ctl(grid_ctx *c)
+{
+    GG_CUDA(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    GG_CUDA(cudaStreamSynchronize(c->stream));
+    return GRID_OK;
+}
+
+int reset_ctl(grid_ctx *c)
+{
+    GG_CUDA(cudaMemsetAsync(c->d_ctl, 0, sizeof(Ctl), c->stream));
+    return GRID_OK;
+}
+
+// ---- grid metadata M -------------------------------------------------------
+// res_a = clamp(ceil(e_a * k), 1, RES_MAX), k = (lambda n / prod_nonzero e)^(1/d)
+// in FP64; scale_a = (float)res_a / e_a in FP32.
+int plan(const float lo[3], const float hi[3], int64_t n, float lambda, grid_info *info)
+{
+    if (n < 0 || !std::isfinite(lambda) || !(lambda > 0.0f)) return GRID_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    float e[3];
+    int d = 0;
+    double vol = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        info->lo[a] = lo[a];
+        info->hi[a] = hi[a];
+        e[a] = hi[a] - lo[a];
+        info->res[a] = 1;
+        info->scale[a] = 0.0f;
+        if (n > 0 && e[a] > 0.0f) {
+            ++d;
+            vol = vol * (double)e[a];
+        }
+    }
+    if (d > 0) {
+        const double q = ((double)lambda * (double)n) / vol;
+        const double k = d == 3 ? std::cbrt(q) : (d == 2 ? std::sqrt(q) : q);
+        for (int a = 0; a < 3; ++a) {
+            if (!(e[a] > 0.0f)) continue;
+            double r = std::ceil((double)e[a] * k);
+            if (!(r >= 1.0)) r = 1.0;
+            if (r > (double)GRID_RES_MAX) r = (double)GRID_RES_MAX;
+            info->res[a] = (int32_t)r;
+            info->scale[a] = (float)info->res[a] / e[a];
+        }
+    }
+    info->n = n;
+    info->ncells = (int64_t)info->res[0] * info->res[1] * info->res[2];
+    info->key_bits = 0;
+    if (info->ncells > 1) {
+        uint64_t m = (uint64_t)(info->ncells - 1);
+        int b = 0;
+        while (m) {
+            ++b;
+            m >>= 1;
+        }
+        info->key_bits = b;
+    }
+    if (info->ncells > kInt32Max) return GRID_EOVERFLOW;
+    return GRID_OK;
+}
+
+// ---- radix-sort pass layout --------------------------------------------------
+struct SortCfg {
+    int passes = 0;
+    int rbits = 8;  // kernel instantiation: widest digit, at least 8
+    int shift[gg::MAX_PASSES] = {0, 0, 0, 0};
+    int bits[gg::MAX_PASSES] = {0, 0, 0, 0};
+};
+
+SortCfg sort_cfg(int key_bits, int rbits_max)
+{
+    SortCfg s;
+    if (key_bits <= 0) return s;
+    s.passes = (key_bits + rbits_max - 1) / rbits_max;
+    int sh = 0, widest = 0;
+    for (int p = 0; p < s.passes; ++p) {
+        const int b = key_bits / s.passes + (p < key_bits % s.passes ? 1 : 0);
+        s.shift[p] = sh;
+        s.bits[p] = b;
+        sh += b;
+        widest = std::max(widest, b);
+    }
+    s.rbits = std::max(8, widest);
+    return s;
+}
+
+unsigned pair_tiles(int64_t count) { return (unsigned)((count + gg::PAIR_TILE - 1) / gg::PAIR_TILE); }
+
+// Radix sort of (keys, vals) over the configured passes.  If gen is set, the
+// first pass generates the object-order pairs from recs/tile_obj; otherwise
+// it reads keys_in/vals_in.  The last pass writes keys_last / vals_last.
+// Returns the buffer holding the sorted keys.
+int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const ObjRec *recs, int64_t nobj,
+               const unsigned *tile_obj, unsigned res_x, unsigned res_y, const unsigned *keys_in,
+               const unsigned *vals_in, unsigned *keys_last, unsigned *vals_last)
+{
+    const unsigned ntiles = pair_tiles(count);
+    const int R = 1 << sc.rbits;
+    const size_t elem = (size_t)count * sizeof(unsigned);
+    GG_TRY(ensure(c, c->status[0], (size_t)ntiles * R * sizeof(unsigned)));
+    if (sc.passes > 1) GG_TRY(ensure(c, c->status[1], (size_t)ntiles * R * sizeof(unsigned)));
+    // intermediate buffers: pass p writes tmp[(P-1-p) % 2 == 0 ? last : scratch]
+    unsigned *ko[gg::MAX_PASSES], *vo[gg::MAX_PASSES];
+    int nscratch_k = 0;
+    for (int p = 0; p < sc.passes; ++p) {
+        const bool to_last = ((sc.passes - 1 - p) % 2) == 0;
+        if (to_last) {
+            ko[p] = keys_last;
+            vo[p] = vals_last;
+        } else {
+            GG_TRY(ensure(c, c->keys[0], elem));
+            GG_TRY(ensure(c, c->vals[0], elem));
+            ko[p] = (unsigned *)c->keys[0].ptr;
+            vo[p] = (unsigned *)c->vals[0].ptr;
+            ++nscratch_k;
+        }
+    }
+    (void)nscratch_k;
+
+    gg::HistArgs h{};
+    h.keys_in = keys_in;
+    h.recs = recs;
+    h.tile_obj = tile_obj;
+    h.res_x = res_x;
+    h.res_y = res_y;
+    h.count = count;
+    h.ntiles = ntiles;
+    h.npasses = sc.passes;
+    for (int p = 0; p < gg::MAX_PASSES; ++p) {
+        h.shift[p] = sc.shift[p];
+        h.bits[p] = sc.bits[p];
+    }
+    h.hist = c->d_hist;
+    h.dbase = c->d_dbase;
+    h.status0 = (unsigned *)c->status[0].ptr;
+    h.status_row = R;
+    h.ctl = c->d_ctl;
+    {
+        KernelScope ks(c, K_HIST, gen ? 16.0 * nobj : 4.0 * count);
+        GG_CUDA(gg::launch_hist(h, sc.rbits, gen ? gg::SRC_GEN : gg::SRC_MEM, c->nsm, c->stream));
+    }
+
+    for (int p = 0; p < sc.passes; ++p) {
+        gg::PassArgs a{};
+        if (p == 0) {
+            a.keys_in = keys_in;
+            a.vals_in = vals_in;
+        } else {
+            a.keys_in = ko[p - 1];
+            a.vals_in = vo[p - 1];
+        }
+        a.recs = recs;
+        a.tile_obj = tile_obj;
+        a.res_x = res_x;
+        a.res_y = res_y;
+        a.keys_out = ko[p];
+        a.vals_out = vo[p];
+        a.count = count;
+        a.shift = sc.shift[p];
+        a.bits = sc.bits[p];
+        a.dbase = c->d_dbase + p * gg::MAX_RADIX;
+        a.status = (unsigned *)c->status[p % 2].ptr;
+        a.status_next = p + 1 < sc.passes ? (unsigned *)c->status[(p + 1) % 2].ptr : nullptr;
+        a.ticket = &c->d_ctl->tickets[1 + p];
+        a.ctl = c->d_ctl;
+        const int src = (p == 0 && gen) ? gg::SRC_GEN : gg::SRC_MEM;
+        KernelScope ks(c, src == gg::SRC_GEN ? K_PASS_GEN : K_PASS,
+                       src == gg::SRC_GEN ? 16.0 * nobj + 8.0 * count : 16.0 * count);
+        GG_CUDA(gg::launch_pass(a, sc.rbits, src, ntiles, c->stream));
+    }
+    return GRID_OK;
+}
+
+bool valid_lambda(float lambda) { return std::isfinite(lambda) && lambda > 0.0f; }
+
+// Output placement for build_core: returns device pointers for cells
+// (ncells + 1) and refs (nrefs).
+struct OutAlloc {
+    virtual int alloc(grid_ctx *c, int64_t ncells1, int64_t nrefs, unsigned **cells, unsigned **refs) = 0;
+    virtual ~OutAlloc() = default;
+};
+
+// BuildParallelGrid (Algorithm 1) on device-resident inputs.
+int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
+               float lambda, grid_info *info, OutAlloc &out)
+{
+    if (n < 0 || nverts < 0 || n > kInt32Max - 1 || !valid_lambda(lambda)) return GRID_EINVAL;
+    if (n > 0 && (!verts || !tris)) return GRID_EINVAL;
+    grid_info I;
+    unsigned *cells = nullptr, *refs = nullptr;
+    if (n == 0) {
+        const float z[3] = {0.f, 0.f, 0.f};
+        GG_TRY(plan(z, z, 0, lambda, &I));
+        GG_TRY(out.alloc(c, 2, 0, &cells, &refs));
+        GG_CUDA(cudaMemsetAsync(cells, 0, 2 * sizeof(unsigned), c->stream));
+        GG_CUDA(cudaStreamSynchronize(c->stream));
+        if (info) *info = I;
+        return GRID_OK;
+    }
+    // a0: boxes + bounds
+    GG_TRY(reset_ctl(c));
+    {
+        KernelScope ks(c, K_BOUNDS, 48.0 * n);
+        GG_CUDA(gg::launch_bounds(verts, nverts, tris, n, c->d_ctl, c->nsm, c->stream));
+    }
+    GG_TRY(read_ctl(c));
+    GG_TRY(ctl_error(c->h_ctl->err));
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = gg::ordered_to_float(~c->h_ctl->lo_inv[a]);
+        hi[a] = gg::ordered_to_float(c->h_ctl->hi_ord[a]);
+    }
+    // a1: M
+    GG_TRY(plan(lo, hi, n, lambda, &I));
+    // a2 + a3: CountCells + ExclusiveSum
+    const int64_t ctiles = (n + gg::COUNT_TILE - 1) / gg::COUNT_TILE;
+    GG_TRY(ensure(c, c->recs, (size_t)n * sizeof(ObjRec)));
+    GG_TRY(ensure(c, c->k2status, (size_t)ctiles * 8));
+    GG_CUDA(cudaMemsetAsync(c->k2status.ptr, 0, (size_t)ctiles * 8, c->stream));
+    gg::CountArgs ca{};
+    ca.verts = verts;
+    ca.nverts = nverts;
+    ca.tris = tris;
+    ca.n = n;
+    for (int a = 0; a < 3; ++a) {
+        ca.lo[a] = I.lo[a];
+        ca.scale[a] = I.scale[a];
+        ca.res[a] = I.res[a];
+    }
+    ca.recs = (ObjRec *)c->recs.ptr;
+    ca.status = (unsigned long long *)c->k2status.ptr;
+    ca.ctl = c->d_ctl;
+    {
+        KernelScope ks(c, K_COUNT, 64.0 * n);
+        GG_CUDA(gg::launch_count_scan(ca, c->stream));
+    }
+    GG_TRY(read_ctl(c));
+    GG_TRY(ctl_error(c->h_ctl->err));
+    const int64_t NO = (int64_t)c->h_ctl->nrefs;
+    if (NO > kInt32Max) return GRID_EOVERFLOW;
+    I.nrefs = NO;
+
+    GG_TRY(out.alloc(c, I.ncells + 1, NO, &cells, &refs));
+    const unsigned count = (unsigned)NO;
+    const SortCfg sc = sort_cfg(I.key_bits, c->rbits_max);
+    if (count > 0) {
+        const unsigned ntiles = pair_tiles(count);
+        GG_TRY(ensure(c, c->tile_obj, (size_t)(ntiles + 1) * sizeof(unsigned)));
+        const ObjRec *recs = (const ObjRec *)c->recs.ptr;
+        unsigned *tile_obj = (unsigned *)c->tile_obj.ptr;
+        {
+            KernelScope ks(c, K_TILES, 4.0 * (ntiles + 1));
+            GG_CUDA(gg::launch_tile_search(recs, n, gg::PAIR_TILE, ntiles, tile_obj, c->stream));
+        }
+        GG_TRY(ensure(c, c->keys[1], (size_t)count * sizeof(unsigned)));
+        unsigned *keys_sorted = (unsigned *)c->keys[1].ptr;
+        if (sc.passes == 0) {
+            gg::EmitArgs ea{};
+            ea.recs = recs;
+            ea.tile_obj = tile_obj;
+            ea.res_x = (unsigned)I.res[0];
+            ea.res_y = (unsigned)I.res[1];
+            ea.count = count;
+            ea.C = keys_sorted;
+            ea.O = refs;
+            KernelScope ks(c, K_EMIT, 16.0 * n + 8.0 * count);
+            GG_CUDA(gg::launch_emit(ea, c->stream));
+        } else {
+            GG_TRY(sort_pairs(c, sc, count, true, recs, n, tile_obj, (unsigned)I.res[0], (unsigned)I.res[1],
+                              nullptr, nullptr, keys_sorted, refs));
+        }
+        gg::ExtractArgs xa{};
+        xa.keys = keys_sorted;
+        xa.count = count;
+        xa.ncells = (unsigned long long)I.ncells;
+        xa.G = cells;
+        xa.ctl = c->d_ctl;
+        KernelScope ks(c, K_EXTRACT, 4.0 * count + 4.0 * (I.ncells + 1));
+        GG_CUDA(gg::launch_extract(xa, c->stream));
+    } else {
+        GG_CUDA(cudaMemsetAsync(cells, 0, (size_t)(I.ncells + 1) * sizeof(unsigned), c->stream));
+    }
+    GG_TRY(read_ctl(c));
+    GG_TRY(ctl_error(c->h_ctl->err));
+    if (info) *info = I;
+    return GRID_OK;
+}
+
+struct PoolOut : OutAlloc {
+    grid_buf *cells_buf, *refs_buf;
+    PoolOut(grid_buf *cb, grid_buf *rb) : cells_buf(cb), refs_buf(rb) {}
+    int alloc(grid_ctx *c, int64_t ncells1, int64_t nrefs, unsigned **cells, unsigned **refs) override
+    {
+        void *pc = nullptr, *pr = nullptr;
+        GG_TRY(pool_alloc(c, (size_t)ncells1 * 4, &pc));
+        int rc = pool_alloc(c, (size_t)nrefs * 4, &pr);
+        if (rc != GRID_OK) {
+            pool_free(c, pc, (size_t)ncells1 * 4);
+            return rc;
+        }
+        cells_buf->ptr = pc;
+        cells_buf->count = ncells1;
+        cells_buf->bytes = (size_t)ncells1 * 4;
+        refs_buf->ptr = pr;
+        refs_buf->count = nrefs;
+        refs_buf->bytes = (size_t)nrefs * 4;
+        *cells = (unsigned *)pc;
+        *refs = (unsigned *)pr;
+        return GRID_OK;
+    }
+};
+
+struct ScratchOut : OutAlloc {
+    int64_t ncells1 = 0, nrefs = 0;
+    int alloc(grid_ctx *c, int64_t nc1, int64_t nr, unsigned **cells, unsigned **refs) override
+    {
+        GG_TRY(ensure(c, c->out_cells, (size_t)nc1 * 4));
+        GG_TRY(ensure(c, c->out_refs, (size_t)std::max<int64_t>(nr, 1) * 4));
+        ncells1 = nc1;
+        nrefs = nr;
+        *cells = (unsigned *)c->out_cells.ptr;
+        *refs = (unsigned *)c->out_refs.ptr;
+        return GRID_OK;
+    }
+};
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+const char *grid_version(void) { return "gb300-grid 0.1 (sm_103a)"; }
+
+const char *grid_strerror(int code)
+{
+    switch (code) {
+    case GRID_OK: return "ok";
+    case GRID_EINVAL: return "invalid argument or input";
+    case GRID_ENOMEM: return "out of memory";
+    case GRID_EOVERFLOW: return "grid too large: ncells or nrefs above INT32_MAX";
+    case GRID_EAGAIN: return "admission refused, retry later";
+    case GRID_ETIMEOUT: return "timed out";
+    case GRID_ECUDA: return "CUDA runtime error";
+    case GRID_ENOSPC: return "host output buffer too small";
+    case GRID_ENOTREADY: return "result not ready";
+    default: return "unknown error";
+    }
+}
+
+int grid_ctx_create(int device, const grid_opts *opts, grid_ctx **out)
+{
+    if (!out) return GRID_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return GRID_EINVAL;
+    }
+    DeviceGuard g(device);
+    grid_ctx *c = new (std::nothrow) grid_ctx();
+    if (!c) return GRID_ENOMEM;
+    c->device = device;
+    if (opts) c->opts = *opts;
+    if (c->opts.radix_bits >= 8 && c->opts.radix_bits <= 11) c->rbits_max = c->opts.radix_bits;
+    int rc = GRID_OK;
+    do {
+        if ((rc = cuda_err(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device)))) break;
+        if ((rc = cuda_err(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking)))) break;
+        c->stream = c->own;
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        if ((rc = cuda_err(cudaMemPoolCreate(&c->pool, &props)))) break;
+        uint64_t thr = UINT64_MAX;
+        if ((rc = cuda_err(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr)))) break;
+        const size_t small = sizeof(Ctl) + 2 * sizeof(unsigned) * gg::MAX_PASSES * gg::MAX_RADIX;
+        void *p = nullptr;
+        if ((rc = cuda_err(cudaMalloc(&p, small)))) break;
+        if ((rc = cuda_err(cudaMemset(p, 0, small)))) break;
+        c->d_ctl = (Ctl *)p;
+        c->d_hist = (unsigned *)((char *)p + sizeof(Ctl));
+        c->d_dbase = c->d_hist + gg::MAX_PASSES * gg::MAX_RADIX;
+        if ((rc = cuda_err(cudaMallocHost(&p, sizeof(Ctl))))) break;
+        c->h_ctl = (Ctl *)p;
+        std::memset(c->h_ctl, 0, sizeof(Ctl));
+    } while (0);
+    if (rc != GRID_OK) {
+        grid_ctx_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return GRID_OK;
+}
+
+void grid_ctx_destroy(grid_ctx *c)
+{
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        Scratch *all[] = {&c->recs, &c->k2status, &c->tile_obj, &c->keys[0], &c->keys[1], &c->vals[0],
+                          &c->vals[1], &c->status[0], &c->status[1], &c->in_verts, &c->in_tris,
+                          &c->out_cells, &c->out_refs};
+        for (Scratch *s : all) release(c, *s);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        resolve_timings(c);
+        for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
+        c->free_events.clear();
+        if (c->d_ctl) cudaFree(c->d_ctl);
+        if (c->h_ctl) cudaFreeHost(c->h_ctl);
+        if (c->pool) cudaMemPoolDestroy(c->pool);
+        if (c->own) cudaStreamDestroy(c->own);
+    }
+    delete c;
+}
+
+int grid_ctx_set_stream(grid_ctx *c, void *stream)
+{
+    if (!c) return GRID_EINVAL;
+    c->stream = stream ? (cudaStream_t)stream : c->own;
+    return GRID_OK;
+}
+
+int grid_ctx_mem_in_use(grid_ctx *c, int64_t *bytes)
+{
+    if (!c || !bytes) return GRID_EINVAL;
+    *bytes = c->in_use.load();
+    return GRID_OK;
+}
+
+int grid_ctx_profile(grid_ctx *c, int enable)
+{
+    if (!c) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    resolve_timings(c);
+    c->profile = enable != 0;
+    for (int k = 0; k < K_NUM; ++k) {
+        c->launches[k] = 0;
+        c->kernel_ms[k] = 0.0;
+        c->kernel_bytes[k] = 0.0;
+    }
+    return GRID_OK;
+}
+
+int grid_ctx_kernel_stats(grid_ctx *c, grid_kernel_stat *out, int max, int *count)
+{
+    if (!c || !count || (max > 0 && !out)) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    GG_CUDA(cudaStreamSynchronize(c->stream));
+    resolve_timings(c);
+    int k2 = 0;
+    for (int k = 0; k < K_NUM && k2 < max; ++k) {
+        if (!c->launches[k]) continue;
+        grid_kernel_stat &o = out[k2++];
+        std::memset(&o, 0, sizeof(o));
+        std::snprintf(o.name, sizeof(o.name), "%s", kKernelNames[k]);
+        o.launches = c->launches[k];
+        o.total_ms = c->kernel_ms[k];
+        o.bytes = c->kernel_bytes[k];
+    }
+    *count = k2;
+    return GRID_OK;
+}
+
+int grid_build(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *tris, int64_t n, float lambda,
+               grid_buf *out_cells, grid_buf *out_refs, grid_info *info)
+{
+    if (!c || !out_cells || !out_refs) return GRID_EINVAL;
+    *out_cells = grid_buf{nullptr, 0, 0};
+    *out_refs = grid_buf{nullptr, 0, 0};
+    DeviceGuard g(c->device);
+    PoolOut po(out_cells, out_refs);
+    int rc = build_core(c, verts, nverts, tris, n, lambda, info, po);
+    if (rc != GRID_OK) {
+        grid_buf_free(c, out_cells);
+        grid_buf_free(c, out_refs);
+    }
+    return rc;
+}
+
+int grid_build_host(grid_ctx *c, const float *h_verts, int64_t nverts, const int32_t *h_tris, int64_t n,
+                    float lambda, int32_t *h_cells, int64_t cells_cap, int32_t *h_refs, int64_t refs_cap,
+                    grid_info *info)
+{
+    if (!c || n < 0 || nverts < 0) return GRID_EINVAL;
+    if (n > 0 && (!h_verts || !h_tris)) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    const size_t vb = (size_t)nverts * 3 * sizeof(float), tb = (size_t)n * 3 * sizeof(int32_t);
+    GG_TRY(ensure(c, c->in_verts, std::max<size_t>(vb, 16)));
+    GG_TRY(ensure(c, c->in_tris, std::max<size_t>(tb, 16)));
+    if (vb) GG_CUDA(cudaMemcpyAsync(c->in_verts.ptr, h_verts, vb, cudaMemcpyHostToDevice, c->stream));
+    if (tb) GG_CUDA(cudaMemcpyAsync(c->in_tris.ptr, h_tris, tb, cudaMemcpyHostToDevice, c->stream));
+    ScratchOut so;
+    grid_info I;
+    GG_TRY(build_core(c, (const float *)c->in_verts.ptr, nverts, (const int32_t *)c->in_tris.ptr, n, lambda,
+                      &I, so));
+    if (info) *info = I;
+    if (!h_cells || !h_refs || cells_cap < so.ncells1 || refs_cap < so.nrefs) return GRID_ENOSPC;
+    GG_CUDA(cudaMemcpyAsync(h_cells, c->out_cells.ptr, (size_t)so.ncells1 * 4, cudaMemcpyDeviceToHost,
+                            c->stream));
+    if (so.nrefs)
+        GG_CUDA(cudaMemcpyAsync(h_refs, c->out_refs.ptr, (size_t)so.nrefs * 4, cudaMemcpyDeviceToHost,
+                                c->stream));
+    GG_CUDA(cudaStreamSynchronize(c->stream));
+    return GRID_OK;
+}
+
+void grid_buf_free(grid_ctx *c, grid_buf *b)
+{
+    if (!c || !b || !b->ptr) return;
+    DeviceGuard g(c->device);
+    pool_free(c, b->ptr, b->bytes);
+    *b = grid_buf{nullptr, 0, 0};
+}
+
+// ---- steps ------------------------------------------------------------------
+
+int grid_bounds(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *tris, int64_t n, float lo[3],
+                float hi[3])
+{
+    if (!c || !lo || !hi || n < 0 || nverts < 0) return GRID_EINVAL;
+    if (n > 0 && (!verts || !tris)) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = 0.0f;
+    if (n == 0) return GRID_OK;
+    GG_TRY(reset_ctl(c));
+    {
+        KernelScope ks(c, K_BOUNDS, 48.0 * n);
+        GG_CUDA(gg::launch_bounds(verts, nverts, tris, n, c->d_ctl, c->nsm, c->stream));
+    }
+    GG_TRY(read_ctl(c));
+    GG_TRY(ctl_error(c->h_ctl->err));
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = gg::ordered_to_float(~c->h_ctl->lo_inv[a]);
+        hi[a] = gg::ordered_to_float(c->h_ctl->hi_ord[a]);
+    }
+    return GRID_OK;
+}
+
+int grid_plan(const float lo[3], const float hi[3], int64_t n, float lambda, grid_info *info)
+{
+    if (!lo || !hi || !info) return GRID_EINVAL;
+    return plan(lo, hi, n, lambda, info);
+}
+
+int grid_count_scan(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
+                    const grid_info *info, grid_objrec *recs, int64_t *nrefs)
+{
+    if (!c || !info || !nrefs || n < 0 || n > kInt32Max - 1 || nverts < 0) return GRID_EINVAL;
+    if (n > 0 && (!verts || !tris || !recs)) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    *nrefs = 0;
+    if (n == 0) return GRID_OK;
+    const int64_t ctiles = (n + gg::COUNT_TILE - 1) / gg::COUNT_TILE;
+    GG_TRY(reset_ctl(c));
+    GG_TRY(ensure(c, c->k2status, (size_t)ctiles * 8));
+    GG_CUDA(cudaMemsetAsync(c->k2status.ptr, 0, (size_t)ctiles * 8, c->stream));
+    gg::CountArgs ca{};
+    ca.verts = verts;
+    ca.nverts = nverts;
+    ca.tris = tris;
+    ca.n = n;
+    for (int a = 0; a < 3; ++a) {
+        ca.lo[a] = info->lo[a];
+        ca.scale[a] = info->scale[a];
+        ca.res[a] = info->res[a];
+    }
+    ca.recs = (ObjRec *)recs;
+    ca.status = (unsigned long long *)c->k2status.ptr;
+    ca.ctl = c->d_ctl;
+    {
+        KernelScope ks(c, K_COUNT, 64.0 * n);
+        GG_CUDA(gg::launch_count_scan(ca, c->stream));
+    }
+    GG_TRY(read_ctl(c));
+    *nrefs = (int64_t)c->h_ctl->nrefs;
+    GG_TRY(ctl_error(c->h_ctl->err));
+    if (*nrefs > kInt32Max) return GRID_EOVERFLOW;
+    return GRID_OK;
+}
+
+int grid_emit_pairs(grid_ctx *c, const grid_objrec *recs, int64_t n, int64_t nrefs, const grid_info *info,
+                    int32_t *C, int32_t *O)
+{
+    if (!c || !info || n < 0 || nrefs < 0 || nrefs > kInt32Max) return GRID_EINVAL;
+    if (nrefs == 0) return GRID_OK;
+    if (n == 0 || !recs || !C || !O) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    const unsigned ntiles = pair_tiles(nrefs);
+    GG_TRY(reset_ctl(c));
+    GG_TRY(ensure(c, c->tile_obj, (size_t)(ntiles + 1) * sizeof(unsigned)));
+    {
+        KernelScope ks(c, K_TILES, 4.0 * (ntiles + 1));
+        GG_CUDA(gg::launch_tile_search((const ObjRec *)recs, n, gg::PAIR_TILE, ntiles,
+                                       (unsigned *)c->tile_obj.ptr, c->stream));
+    }
+    gg::EmitArgs ea{};
+    ea.recs = (const ObjRec *)recs;
+    ea.tile_obj = (const unsigned *)c->tile_obj.ptr;
+    ea.res_x = (unsigned)info->res[0];
+    ea.res_y = (unsigned)info->res[1];
+    ea.count = (unsigned)nrefs;
+    ea.C = (unsigned *)C;
+    ea.O = (unsigned *)O;
+    {
+        KernelScope ks(c, K_EMIT, 16.0 * n + 8.0 * nrefs);
+        GG_CUDA(gg::launch_emit(ea, c->stream));
+    }
+    GG_TRY(read_ctl(c));
+    return ctl_error(c->h_ctl->err);
+}
+
+int grid_sort_pairs(grid_ctx *c, const int32_t *C, const int32_t *O, int64_t count, int32_t key_bits,
+                    int32_t *C_out, int32_t *O_out)
+{
+    if (!c || count < 0 || count > kInt32Max || key_bits < 0 || key_bits > 31) return GRID_EINVAL;
+    if (count == 0) return GRID_OK;
+    if (!C || !O || !C_out || !O_out || C == C_out || O == O_out) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    GG_TRY(reset_ctl(c));
+    const SortCfg sc = sort_cfg(key_bits, c->rbits_max);
+    if (sc.passes == 0) {
+        GG_CUDA(cudaMemcpyAsync(C_out, C, (size_t)count * 4, cudaMemcpyDeviceToDevice, c->stream));
+        GG_CUDA(cudaMemcpyAsync(O_out, O, (size_t)count * 4, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        GG_TRY(sort_pairs(c, sc, (unsigned)count, false, nullptr, 0, nullptr, 0, 0, (const unsigned *)C,
+                          (const unsigned *)O, (unsigned *)C_out, (unsigned *)O_out));
+    }
+    GG_TRY(read_ctl(c));
+    return ctl_error(c->h_ctl->err);
+}
+
+int grid_extract_ranges(grid_ctx *c, const int32_t *C_sorted, int64_t count, int64_t ncells, int32_t *cells)
+{
+    if (!c || count < 0 || count > kInt32Max || ncells < 1 || ncells > kInt32Max || !cells) return GRID_EINVAL;
+    if (count > 0 && !C_sorted) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    GG_TRY(reset_ctl(c));
+    gg::ExtractArgs xa{};
+    xa.keys = (const unsigned *)C_sorted;
+    xa.count = (unsigned long long)count;
+    xa.ncells = (unsigned long long)ncells;
+    xa.G = (unsigned *)cells;
+    xa.ctl = c->d_ctl;
+    {
+        KernelScope ks(c, K_EXTRACT, 4.0 * count + 4.0 * (ncells + 1));
+        GG_CUDA(gg::launch_extract(xa, c->stream));
+    }
+    GG_TRY(read_ctl(c));
+    return ctl_error(c->h_ctl->err);
+}
+
+}  // extern "C"

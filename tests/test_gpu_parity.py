@@ -1,0 +1,279 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Every comparison is exact: the outputs are integer index arrays, and the one
+floating-point decision (world -> cell) is taken in FP32 with the same
+operation order on both sides, so the grids must match bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def assert_grid_equal(g, o, what=""):
+    info = g.info
+    assert tuple(info.res) == tuple(o.plan.res), (what, info.res, o.plan.res)
+    assert np.array_equal(np.array(info.scale, np.float32), o.plan.scale), what
+    assert np.array_equal(np.array(info.lo, np.float32), o.plan.lo), what
+    assert np.array_equal(np.array(info.hi, np.float32), o.plan.hi), what
+    assert info.ncells == o.plan.ncells and info.nrefs == o.NO, (what, info.ncells, info.nrefs, o.NO)
+    G, refs = host(g.cells), host(g.refs)
+    assert G.shape == o.G.shape and refs.shape == o.refs.shape, what
+    bad = np.flatnonzero(G != o.G)
+    assert bad.size == 0, (what, "cells differ", bad[:10], G[bad[:10]], o.G[bad[:10]])
+    bad = np.flatnonzero(refs != o.refs)
+    assert bad.size == 0, (what, "refs differ", bad[:10], refs[bad[:10]], o.refs[bad[:10]])
+
+
+def build_both(ctx, s, method="alg1"):
+    g = ctx.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+    o = oracle.build_grid(s.verts, s.tris, s.lam, method=method)
+    return g, o
+
+
+# ---- step by step ----------------------------------------------------------------
+
+STEP_SCENES = [
+    ("uniform_20k", lambda: scenes.uniform_soup(20_000, seed=101)),
+    ("nonhomog_30k", lambda: scenes.nonhomogeneous_soup(30_000, seed=102, extent=30.0)),
+    ("arch_60k", lambda: scenes.architectural(60_000, seed=103, size=(40.0, 10.0, 40.0), nblobs=40)),
+]
+
+
+@pytest.mark.parametrize("name,make", STEP_SCENES, ids=[n for n, _ in STEP_SCENES])
+def test_steps_match_oracle(ctx, name, make):
+    s = make()
+    v, t = dev(s.verts, torch.float32), dev(s.tris, torch.int32)
+    # a0 boxes / bounds
+    lo, hi = ctx.bounds(v, t)
+    olo, ohi = oracle.bounds(s.verts, s.tris)
+    assert np.array_equal(np.array(lo, np.float32), olo) and np.array_equal(np.array(hi, np.float32), ohi)
+    # a1 metadata
+    import paper_2403_10647_gb300 as pg
+    info = pg.plan(lo, hi, s.n, s.lam)
+    p = oracle.plan(olo, ohi, s.n, s.lam)
+    assert tuple(info.res) == tuple(p.res) and np.array_equal(np.array(info.scale, np.float32), p.scale)
+    # a2 + a3 CountCells + ExclusiveSum
+    recs, nrefs = ctx.count_scan(v, t, info)
+    clo, chi, V = oracle.cell_boxes(s.verts, s.tris, p)
+    off, NO = oracle.exclusive_sum(V)
+    assert nrefs == NO
+    r = host(recs).view(np.uint16).reshape(-1, 8).astype(np.int64)
+    assert np.array_equal(r[:, 0:3], clo) and np.array_equal(r[:, 3:6], chi)
+    assert np.array_equal(host(recs)[:, 3].astype(np.int64) & 0xFFFFFFFF, off)
+    # a4 - a7 object-order pairs
+    info.nrefs = nrefs
+    C, O = ctx.emit_pairs(recs, nrefs, info)
+    oC, oO = oracle.object_order_pairs(clo, chi, off, NO, p.res)
+    assert np.array_equal(host(O), oO) and np.array_equal(host(C), oC)
+    # a8 radix sort
+    Cs, Os = ctx.sort_pairs(C, O, info.key_bits)
+    sC, sO = oracle.sort_pairs(oC, oO)
+    assert np.array_equal(host(Cs), sC) and np.array_equal(host(Os), sO)
+    # a9 ranges
+    G = ctx.extract_ranges(Cs, info.ncells)
+    assert np.array_equal(host(G), oracle.ranges(sC, p.ncells))
+
+
+def test_hand_example_steps(ctx):
+    """The hand-worked Algorithm 1 example, step by step on the GPU."""
+    import _pins
+    import paper_2403_10647_gb300 as pg
+    g = _pins.read_golden("hand_example.txt")
+    verts = np.array(g["verts"], np.float32).reshape(-1, 3)
+    tris = np.array(g["tris"], np.int32).reshape(-1, 3)
+    info = pg.Info(lo=(0.0, 0.0, 0.0), hi=(4.0, 4.0, 1.0), scale=(1.0, 1.0, 1.0), res=(4, 4, 1), key_bits=4,
+                   ncells=16, nrefs=0, n=4)
+    recs, nrefs = ctx.count_scan(dev(verts, torch.float32), dev(tris, torch.int32), info)
+    assert nrefs == int(g["NO"][0])
+    C, O = ctx.emit_pairs(recs, nrefs, info)
+    assert host(C).tolist() == [int(x) for x in g["C_object_order"]]
+    assert host(O).tolist() == [int(x) for x in g["O_object_order"]]
+    Cs, Os = ctx.sort_pairs(C, O, 4)
+    assert host(Cs).tolist() == [int(x) for x in g["C_sorted"]]
+    assert host(Os).tolist() == [int(x) for x in g["O_sorted"]]
+    assert host(ctx.extract_ranges(Cs, 16)).tolist() == [int(x) for x in g["G"]]
+
+
+# ---- the radix sort on its own: sizes spanning tiles and ragged tails ---------------
+
+@pytest.mark.parametrize("count", [1, 2, 31, 4095, 4096, 4097, 3 * 4096 + 17, 250_001, 2_000_003])
+@pytest.mark.parametrize("key_bits", [1, 7, 8, 9, 13, 17, 22, 27, 31])
+def test_sort_pairs(ctx, count, key_bits):
+    g = np.random.Generator(np.random.Philox(count * 64 + key_bits))
+    hi = 1 << key_bits
+    if key_bits > 12 and count > 4096:   # clustered keys with long runs of equal digits
+        C = (g.integers(0, 64, count) * (hi // 64) + g.integers(0, 3, count)).astype(np.int64)
+    else:
+        C = g.integers(0, hi, count).astype(np.int64)
+    C = C.astype(np.int32)
+    O = np.arange(count, dtype=np.int32)[::-1].copy()
+    Cs, Os = ctx.sort_pairs(dev(C, torch.int32), dev(O, torch.int32), key_bits)
+    if count <= 300_000:
+        sC, sO = oracle.sort_pairs(C, O)
+    else:  # stable argsort is the special case the oracle's sort reduces to
+        perm = np.argsort(C, kind="stable")
+        sC, sO = C[perm], O[perm]
+    assert np.array_equal(host(Cs), sC) and np.array_equal(host(Os), sO)
+
+
+@pytest.mark.parametrize("radix_bits", [8, 9, 10, 11])
+def test_radix_widths_agree(radix_bits):
+    import paper_2403_10647_gb300 as pg
+    c = pg.Context(0, radix_bits=radix_bits)
+    try:
+        for s in (scenes.uniform_soup(50_000, seed=7), scenes.nonhomogeneous_soup(40_000, seed=8, extent=35.0)):
+            g, o = build_both(c, s)
+            assert_grid_equal(g, o, f"radix {radix_bits} {s.name}")
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("ncells,count", [(1, 10), (7, 1), (5000, 0), (5000, 3), (100_000, 300_000),
+                                          (3_000_000, 200_000)])
+def test_extract_ranges(ctx, ncells, count):
+    g = np.random.Generator(np.random.Philox(ncells + count))
+    C = np.sort(g.integers(0, ncells, count)).astype(np.int32)
+    G = ctx.extract_ranges(dev(C, torch.int32) if count else torch.zeros(0, dtype=torch.int32, device="cuda"),
+                           ncells)
+    assert np.array_equal(host(G), oracle.ranges(C, ncells))
+
+
+# ---- whole builds ---------------------------------------------------------------------
+
+def test_tiny_scenes(ctx):
+    g = np.random.Generator(np.random.Philox(99))
+    for k in range(60):
+        n = int(g.integers(1, 300))
+        s = scenes.tiny_scene(g, n, box=float(g.uniform(0.5, 50.0)), max_edge=float(g.uniform(0.01, 20.0)))
+        gg, o = build_both(ctx, s)
+        assert_grid_equal(gg, o, f"tiny {k}")
+
+
+@pytest.mark.parametrize("name,make", STEP_SCENES, ids=[n for n, _ in STEP_SCENES])
+def test_build_medium(ctx, name, make):
+    g, o = build_both(ctx, make())
+    assert_grid_equal(g, o, name)
+
+
+def test_deterministic(ctx):
+    s = scenes.nonhomogeneous_soup(100_000, seed=9, extent=46.0)
+    v, t = dev(s.verts, torch.float32), dev(s.tris, torch.int32)
+    a = ctx.build(v, t, s.lam)
+    b = ctx.build(v, t, s.lam)
+    assert torch.equal(a.cells, b.cells) and torch.equal(a.refs, b.refs)
+
+
+def test_build_host_matches_device(ctx):
+    s = scenes.uniform_soup(30_000, seed=10)
+    g = ctx.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+    cells, refs, info = ctx.build_host(torch.from_numpy(s.verts).pin_memory(),
+                                       torch.from_numpy(s.tris).pin_memory(), s.lam)
+    assert np.array_equal(cells.numpy(), host(g.cells)) and np.array_equal(refs.numpy(), host(g.refs))
+    # pageable memory, caller buffers reused
+    cells2, refs2, _ = ctx.build_host(s.verts, s.tris, s.lam, cells_out=cells.clone(), refs_out=refs.clone())
+    assert np.array_equal(cells2.numpy(), cells.numpy()) and np.array_equal(refs2.numpy(), refs.numpy())
+
+
+# ---- edge cases -----------------------------------------------------------------------
+
+def _scene(verts, tris, lam):
+    return scenes.Scene("edge", np.asarray(verts, np.float32).reshape(-1, 3),
+                        np.asarray(tris, np.int32).reshape(-1, 3), lam)
+
+
+def test_empty(ctx):
+    g = ctx.build(torch.zeros((0, 3), device="cuda"), torch.zeros((0, 3), dtype=torch.int32, device="cuda"), 4.0)
+    assert host(g.cells).tolist() == [0, 0] and g.refs.numel() == 0 and tuple(g.info.res) == (1, 1, 1)
+
+
+@pytest.mark.parametrize("case", ["one_tri", "single_cell", "flat_z", "point", "huge_plus_small", "needle"])
+def test_degenerate_scenes(ctx, case):
+    g = np.random.Generator(np.random.Philox(5))
+    if case == "one_tri":
+        s = _scene([[0, 0, 0], [1, 0.5, 0.2], [0.3, 1, 0.9]], [[0, 1, 2]], 64.0)
+    elif case == "single_cell":   # lambda * n / volume < 1: one cell, no sort passes
+        s = _scene(g.random((30, 3)), g.integers(0, 30, (10, 3)), 0.05)
+    elif case == "flat_z":
+        v = g.random((300, 3))
+        v[:, 2] = 0.25
+        s = _scene(v, g.integers(0, 300, (100, 3)), 4.0)
+    elif case == "point":
+        s = _scene(np.full((9, 3), 3.5), [[0, 1, 2], [3, 4, 5], [6, 7, 8]], 4.0)
+    elif case == "huge_plus_small":   # one triangle spans the whole grid
+        v = np.concatenate([[[0, 0, 0], [10, 0, 10], [0, 10, 5]], g.random((3000, 3)) * 10])
+        s = _scene(v, np.concatenate([[[0, 1, 2]], 3 + g.integers(0, 3000, (1000, 3))]), 8.0)
+    else:  # a long thin diagonal triangle (many false intersections, Sec. 5)
+        v = np.concatenate([[[0, 0, 0], [20, 20, 20], [20.01, 20, 20]], g.random((3000, 3)) * 20])
+        s = _scene(v, np.concatenate([[[0, 1, 2]], 3 + g.integers(0, 3000, (1000, 3))]), 4.0)
+    gg, o = build_both(ctx, s)
+    assert_grid_equal(gg, o, case)
+
+
+def test_bad_index_rejected(ctx):
+    import paper_2403_10647_gb300 as pg
+    s = scenes.uniform_soup(1000, seed=3)
+    t = s.tris.copy()
+    t[500, 1] = s.verts.shape[0]
+    with pytest.raises(pg.GridError) as e:
+        ctx.build(dev(s.verts, torch.float32), dev(t, torch.int32), s.lam)
+    assert e.value.code == -1
+    t[500, 1] = -5
+    with pytest.raises(pg.GridError):
+        ctx.build(dev(s.verts, torch.float32), dev(t, torch.int32), s.lam)
+    # the context stays usable
+    g, o = build_both(ctx, s)
+    assert_grid_equal(g, o, "after error")
+
+
+def test_nonfinite_rejected(ctx):
+    import paper_2403_10647_gb300 as pg
+    s = scenes.uniform_soup(1000, seed=4)
+    for bad in (np.nan, np.inf, -np.inf):
+        v = s.verts.copy()
+        v[s.tris[17, 2], 0] = bad
+        with pytest.raises(pg.GridError) as e:
+            ctx.build(dev(v, torch.float32), dev(s.tris, torch.int32), s.lam)
+        assert e.value.code == -1
+
+
+def test_bad_lambda_rejected(ctx):
+    import paper_2403_10647_gb300 as pg
+    s = scenes.uniform_soup(100, seed=4)
+    for lam in (0.0, -1.0, float("nan")):
+        with pytest.raises(pg.GridError):
+            ctx.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), lam)
+
+
+def test_nrefs_overflow_reported(ctx):
+    """Two triangles that each cover all of a 1.7e9-cell grid: NO = 3.5e9
+    exceeds INT32_MAX and the build reports it before allocating pairs."""
+    import paper_2403_10647_gb300 as pg
+    v = [[0, 0, 0], [1, 1, 1], [0, 1, 0], [1, 0, 1], [0, 0, 1], [1, 1, 0]]
+    with pytest.raises(pg.GridError) as e:
+        ctx.build(dev(np.array(v, np.float32), torch.float32), dev(np.array([[0, 1, 2], [3, 4, 5]]), torch.int32),
+                  1200.0 ** 3 / 2)
+    assert e.value.code == -3
+
+
+# ---- the benchmark's workloads at full size ----------------------------------------------
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["uniform_1e5", "nonhomogeneous_1e6", "architectural_1e7"])
+def test_full_size_configs(ctx, name):
+    s = scenes.CONFIGS[name]()
+    g, o = build_both(ctx, s, method="counting")
+    assert_grid_equal(g, o, name)
