@@ -51,16 +51,20 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
-def build_library(force: bool = False, verbose_ptxas: bool = False) -> str:
-    if not force and up_to_date():
+def build_library(force: bool = False, verbose_ptxas: bool = False, out: str | None = None,
+                  defines: tuple = ()) -> str:
+    """Builds the library (into ``out`` if given, with extra -D ``defines``)."""
+    if out is None and not defines and not force and up_to_date():
         return LIB_PATH
+    target = out or LIB_PATH
     os.makedirs(BUILD_DIR, exist_ok=True)
     cc = nvcc()
     pid = os.getpid()
 
     def compile_one(src: str) -> tuple[str, str]:
-        obj = os.path.join(BUILD_DIR, f"{os.path.splitext(src)[0]}.{pid}.o")
-        cmd = [cc] + _flags(verbose_ptxas) + ["-c", os.path.join(CSRC, src), "-o", obj]
+        tag = abs(hash((target, defines))) % 10**8
+        obj = os.path.join(BUILD_DIR, f"{os.path.splitext(src)[0]}.{pid}.{tag}.o")
+        cmd = [cc] + _flags(verbose_ptxas) + [f"-D{d}" for d in defines] + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -72,7 +76,7 @@ def build_library(force: bool = False, verbose_ptxas: bool = False) -> str:
     if verbose_ptxas:
         for _, log in results:
             print(log)
-    tmp = LIB_PATH + f".tmp{pid}"
+    tmp = target + f".tmp{pid}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     for o in objs:
@@ -82,8 +86,8 @@ def build_library(force: bool = False, verbose_ptxas: bool = False) -> str:
             pass
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

@@ -76,26 +76,20 @@ __device__ __forceinline__ T block_excl_sum(T v, T *s_tmp, T *total)
     return wex + inc - v;
 }
 
-// GlobalCoords (Sec. 3) + cell linearisation for pair j of object record r.
-__device__ __forceinline__ unsigned pair_cell(uint4 r, unsigned j, unsigned res_x, unsigned res_y)
-{
-    const unsigned lox = r.x & 0xFFFFu, loy = r.x >> 16, loz = r.y & 0xFFFFu;
-    const unsigned hix = r.y >> 16, hiy = r.z & 0xFFFFu;
-    const unsigned mx = hix - lox + 1u, my = hiy - loy + 1u;
-    const unsigned mxy = mx * my;
-    const unsigned rid = j - r.w;
-    const unsigned z = rid / mxy;
-    const unsigned rem = rid - z * mxy;
-    const unsigned y = rem / mx;
-    const unsigned x = rem - y * mx;
-    return (lox + x) + res_x * ((loy + y) + res_y * (loz + z));
-}
+// Shared-memory index with one pad word per 32: rows written in blocked
+// arrangement (thread t at t * ITEMS + i) and read warp-striped both hit 32
+// distinct banks.
+__device__ __forceinline__ unsigned pad32(unsigned e) { return e + (e >> 5); }
+
+template <int T>
+__host__ __device__ constexpr int padded() { return T + T / 32; }
 
 // MakeObjectIds + InclusiveSum for one pair tile, in shared memory: marks
 // each object whose pair segment starts inside [j0, j0 + cnt) at its start
 // position with its tile-local index, then an inclusive max-scan carries the
-// owning object forward.  After the call mark[e] + *o_first is the object of
-// pair j0 + e.  mark has BLOCK * ITEMS entries; s_tmp BLOCK / 32.
+// owning object forward.  Afterwards mark[pad32(e)] + (returned first object)
+// is the object of pair j0 + e.  mark holds padded<T>() entries; s_tmp
+// BLOCK / 32.
 template <int BLOCK, int ITEMS>
 __device__ __forceinline__ unsigned tile_objects(const ObjRec *__restrict__ recs,
                                                  const unsigned *__restrict__ tile_obj, unsigned t,
@@ -106,19 +100,19 @@ __device__ __forceinline__ unsigned tile_objects(const ObjRec *__restrict__ recs
     constexpr int W = BLOCK / 32;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned of = tile_obj[t], ol = tile_obj[t + 1];
-    for (int p = tid; p < T; p += BLOCK) mark[p] = 0u;
+    for (int p = tid; p < padded<T>(); p += BLOCK) mark[p] = 0u;
     __syncthreads();
     for (unsigned o = of + 1u + tid; o <= ol; o += BLOCK) {
         const unsigned s = __ldg(&recs[o].start);
         const unsigned p = s - j0;
-        if (s >= j0 && p < cnt) mark[p] = o - of;
+        if (s >= j0 && p < cnt) mark[pad32(p)] = o - of;
     }
     __syncthreads();
     unsigned v[ITEMS];
     unsigned m = 0;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        m = max(m, mark[tid * ITEMS + i]);
+        m = max(m, mark[pad32(tid * ITEMS + i)]);
         v[i] = m;
     }
     unsigned inc = warp_incl_max(m);
@@ -134,9 +128,61 @@ __device__ __forceinline__ unsigned tile_objects(const ObjRec *__restrict__ recs
     if (lane == 0) prev = 0u;
     if (w > 0) prev = max(prev, s_tmp[w - 1]);
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) mark[tid * ITEMS + i] = max(v[i], prev);
+    for (int i = 0; i < ITEMS; ++i) mark[pad32(tid * ITEMS + i)] = max(v[i], prev);
     __syncthreads();
     return of;
+}
+
+// SegmentedExclusiveSum + MakeCellIds (GlobalCoords, Sec. 3) for the ITEMS
+// consecutive pairs e = tid * ITEMS + i of a tile (blocked arrangement).  The
+// relative offset rid = j - start is decomposed with divisions only for the
+// thread's first pair: inside a thread's run the pairs of one object are
+// consecutive, and a pair whose object differs from its predecessor's is that
+// object's first pair (rid = 0), so every other pair advances (x, y, z) by one
+// step, x fastest.
+template <int ITEMS>
+__device__ __forceinline__ void gen_blocked(const ObjRec *__restrict__ recs, unsigned of, const unsigned *mark,
+                                            unsigned j0, unsigned cnt, unsigned res_x, unsigned res_y,
+                                            unsigned (&keys)[ITEMS], unsigned (&objs)[ITEMS])
+{
+    const unsigned e0 = threadIdx.x * ITEMS;
+    unsigned o = 0u, x = 0u, y = 0u, z = 0u, mx = 1u, my = 1u, lox = 0u, loy = 0u, loz = 0u;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const unsigned e = e0 + i;
+        keys[i] = 0u;
+        objs[i] = 0u;
+        if (e < cnt) {
+            const unsigned oe = of + mark[pad32(e)];
+            if (i == 0 || oe != o) {
+                o = oe;
+                const uint4 r = __ldg(reinterpret_cast<const uint4 *>(recs) + o);
+                lox = r.x & 0xFFFFu;
+                loy = r.x >> 16;
+                loz = r.y & 0xFFFFu;
+                mx = (r.y >> 16) - lox + 1u;
+                my = (r.z & 0xFFFFu) - loy + 1u;
+                if (i == 0) {
+                    const unsigned rid = j0 + e - r.w;
+                    const unsigned mxy = mx * my;
+                    z = rid / mxy;
+                    const unsigned rem = rid - z * mxy;
+                    y = rem / mx;
+                    x = rem - y * mx;
+                } else {
+                    x = y = z = 0u;
+                }
+            } else if (++x == mx) {
+                x = 0u;
+                if (++y == my) {
+                    y = 0u;
+                    ++z;
+                }
+            }
+            keys[i] = (lox + x) + res_x * ((loy + y) + res_y * (loz + z));
+            objs[i] = o;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -356,20 +402,30 @@ template <int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK) emit_kernel(EmitArgs a)
 {
     constexpr int T = BLOCK * ITEMS;
-    __shared__ unsigned s_mark[T];
+    extern __shared__ __align__(16) unsigned smem[];
+    unsigned *s_mark = smem;                 // [padded T]
+    unsigned *s_obj = smem + padded<T>();    // [padded T]
     __shared__ unsigned s_tmp[BLOCK / 32];
     const unsigned t = blockIdx.x;
     const unsigned j0 = t * (unsigned)T;
     const unsigned cnt = min((unsigned)T, a.count - j0);
     const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
-#pragma unroll 4
+    unsigned keys[ITEMS], objs[ITEMS];
+    gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const unsigned e = threadIdx.x * ITEMS + i;
+        s_mark[pad32(e)] = keys[i];
+        s_obj[pad32(e)] = objs[i];
+    }
+    __syncthreads();
+#pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const unsigned e = i * BLOCK + threadIdx.x;
         if (e < cnt) {
-            const unsigned o = of + s_mark[e];
-            const uint4 r = __ldg(reinterpret_cast<const uint4 *>(a.recs) + o);
-            a.C[j0 + e] = pair_cell(r, j0 + e, a.res_x, a.res_y);
-            a.O[j0 + e] = o;
+            a.C[j0 + e] = s_mark[pad32(e)];
+            a.O[j0 + e] = s_obj[pad32(e)];
         }
     }
 }
@@ -384,8 +440,8 @@ __global__ void __launch_bounds__(BLOCK) hist_kernel(HistArgs a)
     constexpr int T = BLOCK * ITEMS;
     constexpr int R = 1 << RBITS;
     extern __shared__ __align__(16) unsigned smem[];
-    unsigned *s_hist = smem;                          // [npasses][R]
-    unsigned *s_mark = s_hist + MAX_PASSES * R;       // [T] (generated keys only)
+    unsigned *s_hist = smem;                          // [MAX_PASSES][R]
+    unsigned *s_mark = s_hist + MAX_PASSES * R;       // [padded T] (generated keys only)
     __shared__ unsigned s_tmp[BLOCK / 32];
     __shared__ unsigned s_last;
     const int tid = threadIdx.x;
@@ -397,17 +453,9 @@ __global__ void __launch_bounds__(BLOCK) hist_kernel(HistArgs a)
         const unsigned cnt = min((unsigned)T, a.count - j0);
         unsigned keys[ITEMS];
         if (SRC == SRC_GEN) {
+            unsigned objs[ITEMS];
             const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const unsigned e = tid * ITEMS + i;
-                keys[i] = 0u;
-                if (e < cnt) {
-                    const unsigned o = of + s_mark[e];
-                    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(a.recs) + o);
-                    keys[i] = pair_cell(r, j0 + e, a.res_x, a.res_y);
-                }
-            }
+            gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
         } else {
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
@@ -416,23 +464,28 @@ __global__ void __launch_bounds__(BLOCK) hist_kernel(HistArgs a)
             }
         }
         const unsigned nv = cnt > (unsigned)(tid * ITEMS) ? min((unsigned)ITEMS, cnt - tid * ITEMS) : 0u;
+        // the first pass's digit changes with almost every pair: one shared
+        // atomic per pair; higher digits repeat along a thread's run of
+        // consecutive pairs: one atomic per run (predicated, no branches)
+        {
+            const unsigned sh = a.shift[0], mk = (1u << a.bits[0]) - 1u;
 #pragma unroll
-        for (int p = 0; p < MAX_PASSES; ++p) {
+            for (int i = 0; i < ITEMS; ++i)
+                if ((unsigned)i < nv) atomicAdd(&s_hist[(keys[i] >> sh) & mk], 1u);
+        }
+#pragma unroll
+        for (int p = 1; p < MAX_PASSES; ++p) {
             if (p >= a.npasses) break;
             const unsigned sh = a.shift[p], mk = (1u << a.bits[p]) - 1u;
-            unsigned prev = 0xFFFFFFFFu, run = 0u;
+            unsigned prev = (keys[0] >> sh) & mk, run = nv ? 1u : 0u;
 #pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                if ((unsigned)i < nv) {
-                    const unsigned d = (keys[i] >> sh) & mk;
-                    if (d == prev) {
-                        ++run;
-                    } else {
-                        if (run) atomicAdd(&s_hist[p * R + prev], run);
-                        prev = d;
-                        run = 1u;
-                    }
-                }
+            for (int i = 1; i < ITEMS; ++i) {
+                const unsigned d = (keys[i] >> sh) & mk;
+                const bool more = (unsigned)i < nv;
+                const bool flush = more && d != prev;
+                if (flush) atomicAdd(&s_hist[p * R + prev], run);
+                run = flush ? 1u : run + (more ? 1u : 0u);
+                prev = flush ? d : prev;
             }
             if (run) atomicAdd(&s_hist[p * R + prev], run);
         }
@@ -477,163 +530,217 @@ __global__ void __launch_bounds__(BLOCK) hist_kernel(HistArgs a)
 // a8: radix sort - one onesweep-style LSD pass
 // ---------------------------------------------------------------------------
 
-constexpr unsigned LB_PREFIX = 0x80000000u;   // value = inclusive prefix
+
+constexpr unsigned LB_PREFIX = 0x80000000u;   // status word: value = inclusive prefix;
                                               // else value - 1 = tile aggregate; 0 = not ready
+
+// Decoupled look-back for one digit: sums the aggregates of the preceding
+// tiles until one that published its inclusive prefix, reading four
+// predecessors per step so long chains cost a quarter of the round trips.
+// st points at this digit's column (stride R words per tile).  Bounded: past
+// SPIN_LIMIT polls of a not-yet-published word it records ERR_TIMEOUT and
+// returns what it has.
+__device__ __forceinline__ unsigned lookback(const unsigned *st, unsigned R, unsigned tile, Ctl *ctl)
+{
+    unsigned excl = 0;
+    long long k = (long long)tile - 1;
+    unsigned spins = 0;
+    while (k >= 0) {
+        unsigned v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = k - q >= 0 ? ld_relaxed_u32(st + (size_t)(k - q) * R) : LB_PREFIX;
+        int used = 0;
+        bool done = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (done || used < q || v[q] == 0u) continue;   // stop at the first word not published yet
+            if (v[q] & LB_PREFIX) {
+                excl += v[q] & ~LB_PREFIX;
+                done = true;
+            } else {
+                excl += v[q] - 1u;
+            }
+            used = q + 1;
+        }
+        if (done) break;
+        k -= used;
+        if (used == 0) {
+            if (++spins > SPIN_LIMIT) {
+                atomicOr(&ctl->err, ERR_TIMEOUT);
+                break;
+            }
+            if (spins > 4) __nanosleep(32);
+        }
+    }
+    return excl;
+}
+
+// Shared-memory index for 64-bit elements: one pad element per 16, so blocked
+// writes (thread t at t * ITEMS + i) and warp-striped reads are conflict-free.
+__device__ __forceinline__ unsigned pad16(unsigned e) { return e + (e >> 4); }
+
+template <int T>
+__host__ __device__ constexpr int padded16() { return T + T / 16; }
 
 template <int BLOCK, int ITEMS, int RBITS>
 constexpr size_t pass_smem_bytes()
 {
-    return sizeof(unsigned) * (2 * BLOCK * ITEMS + (BLOCK / 32) * ((1 << RBITS) + 1) +
-                               ((1 << RBITS) + 1) + (1 << RBITS) + BLOCK / 32 + 4);
+    return sizeof(unsigned long long) * padded16<BLOCK * ITEMS>() +
+           sizeof(unsigned) * (4 * (BLOCK / 32) * (1 << RBITS) + ((1 << RBITS) + 1) + (1 << RBITS) + BLOCK / 32 + 4);
 }
 
-template <int BLOCK, int ITEMS, int RBITS, int SRC>
-__global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a)
+__device__ __forceinline__ unsigned long long pack_kv(unsigned k, unsigned v)
+{
+    return ((unsigned long long)k << 32) | v;
+}
+
+template <int BLOCK, int ITEMS, int RBITS, int IN, int OUT>
+__global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) pass_kernel(PassArgs a)
 {
     constexpr int W = BLOCK / 32;
     constexpr int T = BLOCK * ITEMS;
     constexpr int R = 1 << RBITS;
-    constexpr int RW = R + 1;                 // one extra bucket for the tail of the last tile
-    static_assert(R % BLOCK == 0, "digits per thread");
-    extern __shared__ __align__(16) unsigned smem[];
-    unsigned *s_keys = smem;                  // [T]  (aliases the object marks while generating)
-    unsigned *s_vals = s_keys + T;            // [T]
-    unsigned *s_whist = s_vals + T;           // [W][R + 1]
-    unsigned *s_dstart = s_whist + W * RW;    // [R + 1]
-    unsigned *s_gbase = s_dstart + RW;        // [R]
-    unsigned *s_tmp = s_gbase + R;            // [W]
-    unsigned *s_misc = s_tmp + W;             // [4]
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *s_elem = reinterpret_cast<unsigned long long *>(smem_raw);   // [padded16 T]
+    unsigned *s_mark = reinterpret_cast<unsigned *>(smem_raw);   // object marks while generating (aliases s_elem)
+    unsigned *s_whist = reinterpret_cast<unsigned *>(s_elem + padded16<T>());      // [W][R] warp digit counts
+    unsigned *s_wmask = s_whist + W * R;        // [3][W][R] peer masks, three rotating buffers
+    unsigned *s_dstart = s_wmask + 3 * W * R;   // [R + 1]
+    unsigned *s_gbase = s_dstart + R + 1;       // [R]
+    unsigned *s_tmp = s_gbase + R;              // [W]
+    unsigned *s_misc = s_tmp + W;               // [4]
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) s_misc[0] = atomicAdd(a.ticket, 1u);
-    for (int i = tid; i < W * RW; i += BLOCK) s_whist[i] = 0u;
+    for (int i = tid; i < 4 * W * R; i += BLOCK) s_whist[i] = 0u;
     __syncthreads();
     const unsigned tile = s_misc[0];
     const unsigned j0 = tile * (unsigned)T;
     const unsigned cnt = min((unsigned)T, a.count - j0);
     const unsigned sh = a.shift, mk = (1u << a.bits) - 1u;
 
-    unsigned keys[ITEMS], vals[ITEMS];
-    if (SRC == SRC_GEN) {
-        const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, tile, j0, cnt, s_keys, s_tmp);
+    // element of item i for this lane (warp-striped): e = w * 32 * ITEMS + i * 32 + lane
+    unsigned long long el[ITEMS];
+    if (IN == IN_GEN) {
+        unsigned keys[ITEMS], objs[ITEMS];
+        const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, tile, j0, cnt, s_mark, s_tmp);
+        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) s_elem[pad16(tid * ITEMS + i)] = pack_kv(keys[i], objs[i]);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) el[i] = s_elem[pad16(w * 32 * ITEMS + i * 32 + lane)];
+    } else if (IN == IN_PAIR) {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-            keys[i] = 0u;
-            vals[i] = 0u;
-            if (e < cnt) {
-                const unsigned o = of + s_keys[e];
-                const uint4 r = __ldg(reinterpret_cast<const uint4 *>(a.recs) + o);
-                keys[i] = pair_cell(r, j0 + e, a.res_x, a.res_y);
-                vals[i] = o;
-            }
+            el[i] = e < cnt ? pack_kv(__ldcs(a.keys_in + j0 + e), __ldcs(a.vals_in + j0 + e)) : 0ull;
         }
     } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-            keys[i] = e < cnt ? __ldcs(a.keys_in + j0 + e) : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-            vals[i] = e < cnt ? __ldcs(a.vals_in + j0 + e) : 0u;
+            el[i] = e < cnt ? __ldcs(a.elems_in + j0 + e) : 0ull;
         }
     }
 
-    // warp-level multisplit: rank of each element among equal digits, in
-    // element order (items in order, lanes in order)
-    unsigned ranks[ITEMS];
-    unsigned *wh = s_whist + w * RW;
+    // warp-level multisplit, stable in element order (items in order, lanes in
+    // order): the lanes holding digit d find each other by OR-ing their lane
+    // bit into a shared mask word for d; the lowest of them reserves the
+    // group's slots in the warp's digit count with one shared atomic and the
+    // old count is broadcast.  Three mask buffers rotate so a buffer is
+    // cleared one item after its use and reused one item later, with a single
+    // warp barrier per item.
+    static_assert(ITEMS % 2 == 0 && T <= 65536, "ranks are packed in 16-bit pairs");
+    unsigned ranks[ITEMS / 2];   // 16-bit ranks, two per register
+    unsigned *wh = s_whist + w * R;
     const unsigned ltmask = lanemask_lt();
+    const unsigned bit = 1u << lane;
+    unsigned clear_d = 0u;
+    bool clear_me = false;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-        const unsigned d = e < cnt ? (keys[i] >> sh) & mk : (unsigned)R;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const unsigned before = wh[d];
+        const bool ok = e < cnt;
+        const unsigned d = (unsigned)(el[i] >> 32 >> sh) & mk;
+        unsigned *wm = s_wmask + (i % 3) * W * R + w * R;
+        if (ok) atomicOr(&wm[d], bit);
+        __syncwarp();
+        if (clear_me) s_wmask[((i + 2) % 3) * W * R + w * R + clear_d] = 0u;   // previous item's word
+        const unsigned peers = ok ? wm[d] : 0u;
         const unsigned lt = __popc(peers & ltmask);
-        __syncwarp();
-        if (lt == 0) wh[d] = before + __popc(peers);
-        __syncwarp();
-        ranks[i] = before + lt;
+        const bool leader = ok && lt == 0u;
+        unsigned old = 0u;
+        if (leader) old = atomicAdd(&wh[d], __popc(peers));
+        old = __shfl_sync(0xffffffffu, old, ok ? __ffs(peers) - 1 : lane);
+        if (i % 2 == 0)
+            ranks[i / 2] = old + lt;
+        else
+            ranks[i / 2] |= (old + lt) << 16;
+        clear_me = leader;
+        clear_d = d;
     }
+    __syncwarp();
+    if (clear_me) s_wmask[((ITEMS + 2) % 3) * W * R + w * R + clear_d] = 0u;
     __syncthreads();
 
-    // per digit: exclusive offsets across warps, tile count, publish aggregate
-    for (int d = tid; d < RW; d += BLOCK) {
+    // per digit: exclusive offsets across warps and the tile's count; the
+    // aggregate is published and the look-back run at once, so the inclusive
+    // prefix reaches the following tiles as early as possible
+    for (int d = tid; d < R; d += BLOCK) {
         unsigned sum = 0;
 #pragma unroll
         for (int ww = 0; ww < W; ++ww) {
-            const unsigned c = s_whist[ww * RW + d];
-            s_whist[ww * RW + d] = sum;
+            const unsigned c = s_whist[ww * R + d];
+            s_whist[ww * R + d] = sum;
             sum += c;
         }
-        s_dstart[d] = sum;
-        if (d < R) {
-            unsigned *st = a.status + (size_t)tile * R + d;
-            st_relaxed_u32(st, tile == 0 ? (LB_PREFIX | sum) : sum + 1u);
+        unsigned *st = a.status + (size_t)tile * R + d;
+        unsigned excl = 0;
+        if (tile == 0) {
+            st_relaxed_u32(st, LB_PREFIX | sum);
+        } else {
+            st_relaxed_u32(st, sum + 1u);
+            excl = lookback(a.status + d, R, tile, a.ctl);
+            st_relaxed_u32(st, LB_PREFIX | (excl + sum));
         }
+        s_dstart[d] = sum;
+        s_gbase[d] = a.dbase[d] + excl;
+        if (a.status_next) a.status_next[(size_t)tile * R + d] = 0u;
     }
     __syncthreads();
     // exclusive scan of the tile's digit counts -> local digit starts
     {
-        constexpr int C = R / BLOCK;
+        constexpr int C = (R + BLOCK - 1) / BLOCK;   // digits per thread
         unsigned loc[C];
         unsigned s = 0;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            loc[k] = s_dstart[tid * C + k];
+            loc[k] = tid * C + k < R ? s_dstart[tid * C + k] : 0u;
             s += loc[k];
         }
         unsigned tot;
         unsigned ex = block_excl_sum<BLOCK>(s, s_tmp, &tot);
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            s_dstart[tid * C + k] = ex;
+            if (tid * C + k < R) {
+                s_dstart[tid * C + k] = ex;
+                s_gbase[tid * C + k] -= ex;   // global start of the digit's run minus its local start
+            }
             ex += loc[k];
         }
-        if (tid == 0) s_dstart[R] = tot;
     }
     __syncthreads();
     // stage the tile in shared memory in locally sorted order
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-        const unsigned d = e < cnt ? (keys[i] >> sh) & mk : (unsigned)R;
-        const unsigned pos = s_dstart[d] + s_whist[w * RW + d] + ranks[i];
-        s_keys[pos] = keys[i];
-        s_vals[pos] = vals[i];
-    }
-    // decoupled look-back per digit
-    for (int d = tid; d < R; d += BLOCK) {
-        const unsigned cntd = s_dstart[d + 1] - s_dstart[d];
-        unsigned excl = 0;
-        if (tile > 0) {
-            const unsigned *st = a.status + d;
-            long long k = (long long)tile - 1;
-            unsigned spins = 0;
-            while (k >= 0) {
-                const unsigned v = ld_relaxed_u32(st + (size_t)k * R);
-                if (v == 0u) {
-                    if (++spins > SPIN_LIMIT) {
-                        atomicOr(&a.ctl->err, ERR_TIMEOUT);
-                        break;
-                    }
-                    if (spins > 8) __nanosleep(32);
-                    continue;
-                }
-                if (v & LB_PREFIX) {
-                    excl += v & ~LB_PREFIX;
-                    break;
-                }
-                excl += v - 1u;
-                --k;
-            }
-            st_relaxed_u32(a.status + (size_t)tile * R + d, LB_PREFIX | (excl + cntd));
+        if (e < cnt) {
+            const unsigned d = (unsigned)(el[i] >> 32 >> sh) & mk;
+            const unsigned rk = (ranks[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
+            s_elem[s_dstart[d] + s_whist[w * R + d] + rk] = el[i];
         }
-        s_gbase[d] = a.dbase[d] + excl - s_dstart[d];
-        if (a.status_next) a.status_next[(size_t)tile * R + d] = 0u;
     }
     __syncthreads();
     // scatter: consecutive threads write consecutive positions of a digit run
@@ -642,11 +749,15 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a)
     for (int i = 0; i < ITEMS; ++i) {
         const unsigned pos = i * BLOCK + tid;
         if (pos < cnt) {
-            const unsigned k = s_keys[pos];
-            const unsigned dst = s_gbase[(k >> sh) & mk] + pos;
+            const unsigned long long v = s_elem[pos];
+            const unsigned dst = s_gbase[(unsigned)(v >> 32 >> sh) & mk] + pos;
             if (dst < a.count) {
-                __stcg(a.keys_out + dst, k);
-                __stcg(a.vals_out + dst, s_vals[pos]);
+                if (OUT == OUT_PACKED) {
+                    __stcg(a.elems_out + dst, v);
+                } else {
+                    __stcg(a.keys_out + dst, (unsigned)(v >> 32));
+                    __stcg(a.vals_out + dst, (unsigned)v);
+                }
             } else {
                 bad = true;
             }
@@ -660,22 +771,32 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a)
 // ---------------------------------------------------------------------------
 
 // Merge order: cell c precedes key k iff c <= k, so G[c] = number of keys
-// before cell c in the merged sequence = number of keys < c.
+// before cell c in the merged sequence = number of keys < c.  Returns the
+// number of keys among the first d merged items.
 __device__ __forceinline__ unsigned long long merge_split(const unsigned *keys, unsigned long long nA,
-                                                          unsigned long long nB, unsigned long long d,
-                                                          unsigned long long c_base)
+                                                          unsigned long long nB, unsigned long long d)
 {
     unsigned long long lo = d > nB ? d - nB : 0ull;
     unsigned long long hi = d < nA ? d : nA;
     while (lo < hi) {
         const unsigned long long mid = (lo + hi) >> 1;
         // key[mid] precedes cell (d - mid - 1)?
-        if ((unsigned long long)keys[mid] < c_base + (d - mid - 1ull))
+        if ((unsigned long long)__ldg(keys + mid) < d - mid - 1ull)
             lo = mid + 1ull;
         else
             hi = mid;
     }
     return lo;
+}
+
+// The split of every extraction block's first diagonal, all in parallel.
+__global__ void __launch_bounds__(256) extract_split_kernel(ExtractArgs a, unsigned long long nblocks)
+{
+    const unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nblocks) return;
+    const unsigned long long nA = a.count, nB = a.ncells + 1ull;
+    const unsigned long long d = min(b * (unsigned long long)EXTRACT_TILE, nA + nB);
+    a.splits[b] = (unsigned)merge_split(a.keys, nA, nB, d);
 }
 
 template <int BLOCK, int ITEMS>
@@ -684,15 +805,12 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
     constexpr int D = BLOCK * ITEMS;
     __shared__ unsigned s_keys[D];
     __shared__ unsigned s_G[D];
-    __shared__ unsigned long long s_split[2];
     const int tid = threadIdx.x;
     const unsigned long long nA = a.count, nB = a.ncells + 1ull;
     const unsigned long long M = nA + nB;
     const unsigned long long d0 = (unsigned long long)blockIdx.x * D;
     const unsigned long long d1 = min(d0 + D, M);
-    if (tid < 2) s_split[tid] = merge_split(a.keys, nA, nB, tid == 0 ? d0 : d1, 0ull);
-    __syncthreads();
-    const unsigned long long i0 = s_split[0], i1 = s_split[1];
+    const unsigned long long i0 = a.splits[blockIdx.x], i1 = a.splits[blockIdx.x + 1];
     const unsigned long long c0 = d0 - i0, c1 = d1 - i1;
     const unsigned na = (unsigned)(i1 - i0), nb = (unsigned)(c1 - c0);
     for (unsigned k = tid; k < na; k += BLOCK) s_keys[k] = __ldcs(a.keys + i0 + k);
@@ -719,7 +837,7 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
                 s_G[ib] = (unsigned)(i0 + ia);
                 ++ib;
             } else {
-                if (s_keys[ia] >= a.ncells) bad = 1u;
+                if (ia < na && s_keys[ia] >= a.ncells) bad = 1u;
                 ++ia;
             }
         }
@@ -764,7 +882,15 @@ cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s)
 {
     if (a.count == 0) return cudaSuccess;
     const unsigned tiles = (a.count + PAIR_TILE - 1) / PAIR_TILE;
-    emit_kernel<PAIR_BLOCK, PAIR_TILE / PAIR_BLOCK><<<tiles, PAIR_BLOCK, 0, s>>>(a);
+    auto k = emit_kernel<PAIR_BLOCK, PAIR_TILE / PAIR_BLOCK>;
+    const size_t smem = 2 * sizeof(unsigned) * padded<PAIR_TILE>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k<<<tiles, PAIR_BLOCK, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -773,7 +899,7 @@ static cudaError_t launch_hist_t(const HistArgs &a, int nsm, cudaStream_t s)
 {
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
     auto k = hist_kernel<PAIR_BLOCK, ITEMS, RBITS, SRC>;
-    const size_t smem = sizeof(unsigned) * (MAX_PASSES * (1 << RBITS) + (SRC == SRC_GEN ? PAIR_TILE : 0));
+    const size_t smem = sizeof(unsigned) * (MAX_PASSES * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -788,11 +914,11 @@ static cudaError_t launch_hist_t(const HistArgs &a, int nsm, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int RBITS, int SRC>
+template <int RBITS, int IN, int OUT>
 static cudaError_t launch_pass_t(const PassArgs &a, unsigned ntiles, cudaStream_t s)
 {
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
-    auto k = pass_kernel<PAIR_BLOCK, ITEMS, RBITS, SRC>;
+    auto k = pass_kernel<PAIR_BLOCK, ITEMS, RBITS, IN, OUT>;
     constexpr size_t smem = pass_smem_bytes<PAIR_BLOCK, ITEMS, RBITS>();
     static bool configured = false;
     if (!configured) {
@@ -802,6 +928,17 @@ static cudaError_t launch_pass_t(const PassArgs &a, unsigned ntiles, cudaStream_
     }
     k<<<ntiles, PAIR_BLOCK, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int RBITS>
+static cudaError_t launch_pass_r(const PassArgs &a, int in, int out, unsigned ntiles, cudaStream_t s)
+{
+    if (in == IN_GEN) return out == OUT_PACKED ? launch_pass_t<RBITS, IN_GEN, OUT_PACKED>(a, ntiles, s)
+                                               : launch_pass_t<RBITS, IN_GEN, OUT_PAIR>(a, ntiles, s);
+    if (in == IN_PAIR) return out == OUT_PACKED ? launch_pass_t<RBITS, IN_PAIR, OUT_PACKED>(a, ntiles, s)
+                                                : launch_pass_t<RBITS, IN_PAIR, OUT_PAIR>(a, ntiles, s);
+    return out == OUT_PACKED ? launch_pass_t<RBITS, IN_PACKED, OUT_PACKED>(a, ntiles, s)
+                             : launch_pass_t<RBITS, IN_PACKED, OUT_PAIR>(a, ntiles, s);
 }
 
 cudaError_t launch_hist(const HistArgs &a, int rbits, int src, int nsm, cudaStream_t s)
@@ -822,29 +959,34 @@ cudaError_t launch_hist(const HistArgs &a, int rbits, int src, int nsm, cudaStre
 #undef GG_HIST
 }
 
-cudaError_t launch_pass(const PassArgs &a, int rbits, int src, unsigned ntiles, cudaStream_t s)
+cudaError_t launch_pass(const PassArgs &a, int rbits, int in, int out, unsigned ntiles, cudaStream_t s)
 {
     if (ntiles == 0) return cudaSuccess;
-#define GG_PASS(RB)                                                        \
-    case RB:                                                               \
-        return src == SRC_GEN ? launch_pass_t<RB, SRC_GEN>(a, ntiles, s)  \
-                              : launch_pass_t<RB, SRC_MEM>(a, ntiles, s);
     switch (rbits) {
-        GG_PASS(8)
-        GG_PASS(9)
-        GG_PASS(10)
-        GG_PASS(11)
-    default:
-        return cudaErrorInvalidValue;
+    case 8: return launch_pass_r<8>(a, in, out, ntiles, s);
+    case 9: return launch_pass_r<9>(a, in, out, ntiles, s);
+    case 10: return launch_pass_r<10>(a, in, out, ntiles, s);
+    case 11: return launch_pass_r<11>(a, in, out, ntiles, s);
+    default: return cudaErrorInvalidValue;
     }
-#undef GG_PASS
+}
+
+unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells)
+{
+    return (count + ncells + 1ull + EXTRACT_TILE - 1) / EXTRACT_TILE;
+}
+
+cudaError_t launch_extract_split(const ExtractArgs &a, cudaStream_t s)
+{
+    const unsigned long long nb = extract_blocks(a.count, a.ncells);
+    extract_split_kernel<<<(unsigned)((nb + 1 + 255) / 256), 256, 0, s>>>(a, nb);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_extract(const ExtractArgs &a, cudaStream_t s)
 {
-    const unsigned long long M = a.count + a.ncells + 1ull;
-    const unsigned long long blocks = (M + EXTRACT_TILE - 1) / EXTRACT_TILE;
-    extract_kernel<EXTRACT_BLOCK, EXTRACT_TILE / EXTRACT_BLOCK><<<(unsigned)blocks, EXTRACT_BLOCK, 0, s>>>(a);
+    const unsigned long long nb = extract_blocks(a.count, a.ncells);
+    extract_kernel<EXTRACT_BLOCK, EXTRACT_TILE / EXTRACT_BLOCK><<<(unsigned)nb, EXTRACT_BLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -43,9 +43,9 @@ struct Scratch {
     size_t bytes = 0;
 };
 
-enum KernelId { K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_HIST, K_PASS_GEN, K_PASS, K_EXTRACT, K_NUM };
-const char *const kKernelNames[K_NUM] = {"bounds", "count_scan", "tile_search", "emit",
-                                         "hist", "pass_gen", "pass", "extract"};
+enum KernelId { K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_HIST, K_PASS_GEN, K_PASS, K_SPLIT, K_EXTRACT, K_NUM };
+const char *const kKernelNames[K_NUM] = {"bounds", "count_scan", "tile_search", "emit", "hist",
+                                         "pass_gen", "pass", "extract_split", "extract"};
 
 struct PendingTiming {
     int kid;
@@ -68,7 +68,7 @@ struct grid_ctx {
     unsigned *d_hist = nullptr;  // [MAX_PASSES][MAX_RADIX], kept zero between uses
     unsigned *d_dbase = nullptr; // [MAX_PASSES][MAX_RADIX]
 
-    Scratch recs, k2status, tile_obj, keys[2], vals[2], status[2];
+    Scratch recs, k2status, tile_obj, keys_sorted, packed[2], status[2], splits;
     Scratch in_verts, in_tris, out_cells, out_refs;  // host-buffer builds
     std::atomic<int64_t> in_use{0};
 
@@ -306,27 +306,13 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
 {
     const unsigned ntiles = pair_tiles(count);
     const int R = 1 << sc.rbits;
-    const size_t elem = (size_t)count * sizeof(unsigned);
+    const size_t packed_bytes = (size_t)count * sizeof(unsigned long long);
     GG_TRY(ensure(c, c->status[0], (size_t)ntiles * R * sizeof(unsigned)));
-    if (sc.passes > 1) GG_TRY(ensure(c, c->status[1], (size_t)ntiles * R * sizeof(unsigned)));
-    // intermediate buffers: pass p writes tmp[(P-1-p) % 2 == 0 ? last : scratch]
-    unsigned *ko[gg::MAX_PASSES], *vo[gg::MAX_PASSES];
-    int nscratch_k = 0;
-    for (int p = 0; p < sc.passes; ++p) {
-        const bool to_last = ((sc.passes - 1 - p) % 2) == 0;
-        if (to_last) {
-            ko[p] = keys_last;
-            vo[p] = vals_last;
-        } else {
-            GG_TRY(ensure(c, c->keys[0], elem));
-            GG_TRY(ensure(c, c->vals[0], elem));
-            ko[p] = (unsigned *)c->keys[0].ptr;
-            vo[p] = (unsigned *)c->vals[0].ptr;
-            ++nscratch_k;
-        }
+    if (sc.passes > 1) {
+        GG_TRY(ensure(c, c->status[1], (size_t)ntiles * R * sizeof(unsigned)));
+        GG_TRY(ensure(c, c->packed[0], packed_bytes));
     }
-    (void)nscratch_k;
-
+    if (sc.passes > 2) GG_TRY(ensure(c, c->packed[1], packed_bytes));
     gg::HistArgs h{};
     h.keys_in = keys_in;
     h.recs = recs;
@@ -350,21 +336,23 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         GG_CUDA(gg::launch_hist(h, sc.rbits, gen ? gg::SRC_GEN : gg::SRC_MEM, c->nsm, c->stream));
     }
 
+    // pass p reads packed[(p - 1) % 2] and writes packed[p % 2]; the first
+    // pass generates or reads two arrays, the last writes two arrays
     for (int p = 0; p < sc.passes; ++p) {
         gg::PassArgs a{};
-        if (p == 0) {
-            a.keys_in = keys_in;
-            a.vals_in = vals_in;
-        } else {
-            a.keys_in = ko[p - 1];
-            a.vals_in = vo[p - 1];
-        }
+        const bool last = p == sc.passes - 1;
+        const int in = p > 0 ? gg::IN_PACKED : (gen ? gg::IN_GEN : gg::IN_PAIR);
+        const int out = last ? gg::OUT_PAIR : gg::OUT_PACKED;
+        a.keys_in = keys_in;
+        a.vals_in = vals_in;
+        if (p > 0) a.elems_in = (const unsigned long long *)c->packed[(p - 1) % 2].ptr;
         a.recs = recs;
         a.tile_obj = tile_obj;
         a.res_x = res_x;
         a.res_y = res_y;
-        a.keys_out = ko[p];
-        a.vals_out = vo[p];
+        if (!last) a.elems_out = (unsigned long long *)c->packed[p % 2].ptr;
+        a.keys_out = keys_last;
+        a.vals_out = vals_last;
         a.count = count;
         a.shift = sc.shift[p];
         a.bits = sc.bits[p];
@@ -373,15 +361,36 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         a.status_next = p + 1 < sc.passes ? (unsigned *)c->status[(p + 1) % 2].ptr : nullptr;
         a.ticket = &c->d_ctl->tickets[1 + p];
         a.ctl = c->d_ctl;
-        const int src = (p == 0 && gen) ? gg::SRC_GEN : gg::SRC_MEM;
-        KernelScope ks(c, src == gg::SRC_GEN ? K_PASS_GEN : K_PASS,
-                       src == gg::SRC_GEN ? 16.0 * nobj + 8.0 * count : 16.0 * count);
-        GG_CUDA(gg::launch_pass(a, sc.rbits, src, ntiles, c->stream));
+        KernelScope ks(c, in == gg::IN_GEN ? K_PASS_GEN : K_PASS,
+                       in == gg::IN_GEN ? 16.0 * nobj + 8.0 * count : 16.0 * count);
+        GG_CUDA(gg::launch_pass(a, sc.rbits, in, out, ntiles, c->stream));
     }
     return GRID_OK;
 }
 
 bool valid_lambda(float lambda) { return std::isfinite(lambda) && lambda > 0.0f; }
+
+// RunLengthEncode + NonEmptyCells + ExclusiveSum: merge-path splits, then the
+// per-block merge of sorted keys against cell ids.
+int extract_ranges(grid_ctx *c, const unsigned *keys, int64_t count, int64_t ncells, unsigned *cells)
+{
+    const unsigned long long nb = gg::extract_blocks((unsigned long long)count, (unsigned long long)ncells);
+    GG_TRY(ensure(c, c->splits, (size_t)(nb + 1) * sizeof(unsigned)));
+    gg::ExtractArgs xa{};
+    xa.keys = keys;
+    xa.count = (unsigned long long)count;
+    xa.ncells = (unsigned long long)ncells;
+    xa.G = cells;
+    xa.splits = (unsigned *)c->splits.ptr;
+    xa.ctl = c->d_ctl;
+    {
+        KernelScope ks(c, K_SPLIT, 4.0 * (nb + 1));
+        GG_CUDA(gg::launch_extract_split(xa, c->stream));
+    }
+    KernelScope ks(c, K_EXTRACT, 4.0 * count + 4.0 * (ncells + 1));
+    GG_CUDA(gg::launch_extract(xa, c->stream));
+    return GRID_OK;
+}
 
 // Output placement for build_core: returns device pointers for cells
 // (ncells + 1) and refs (nrefs).
@@ -462,8 +471,8 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
             KernelScope ks(c, K_TILES, 4.0 * (ntiles + 1));
             GG_CUDA(gg::launch_tile_search(recs, n, gg::PAIR_TILE, ntiles, tile_obj, c->stream));
         }
-        GG_TRY(ensure(c, c->keys[1], (size_t)count * sizeof(unsigned)));
-        unsigned *keys_sorted = (unsigned *)c->keys[1].ptr;
+        GG_TRY(ensure(c, c->keys_sorted, (size_t)count * sizeof(unsigned)));
+        unsigned *keys_sorted = (unsigned *)c->keys_sorted.ptr;
         if (sc.passes == 0) {
             gg::EmitArgs ea{};
             ea.recs = recs;
@@ -479,14 +488,7 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
             GG_TRY(sort_pairs(c, sc, count, true, recs, n, tile_obj, (unsigned)I.res[0], (unsigned)I.res[1],
                               nullptr, nullptr, keys_sorted, refs));
         }
-        gg::ExtractArgs xa{};
-        xa.keys = keys_sorted;
-        xa.count = count;
-        xa.ncells = (unsigned long long)I.ncells;
-        xa.G = cells;
-        xa.ctl = c->d_ctl;
-        KernelScope ks(c, K_EXTRACT, 4.0 * count + 4.0 * (I.ncells + 1));
-        GG_CUDA(gg::launch_extract(xa, c->stream));
+        GG_TRY(extract_ranges(c, keys_sorted, count, I.ncells, cells));
     } else {
         GG_CUDA(cudaMemsetAsync(cells, 0, (size_t)(I.ncells + 1) * sizeof(unsigned), c->stream));
     }
@@ -612,8 +614,8 @@ void grid_ctx_destroy(grid_ctx *c)
     {
         DeviceGuard g(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
-        Scratch *all[] = {&c->recs, &c->k2status, &c->tile_obj, &c->keys[0], &c->keys[1], &c->vals[0],
-                          &c->vals[1], &c->status[0], &c->status[1], &c->in_verts, &c->in_tris,
+        Scratch *all[] = {&c->recs, &c->k2status, &c->tile_obj, &c->splits, &c->keys_sorted, &c->packed[0],
+                          &c->packed[1], &c->status[0], &c->status[1], &c->in_verts, &c->in_tris,
                           &c->out_cells, &c->out_refs};
         for (Scratch *s : all) release(c, *s);
         if (c->stream) cudaStreamSynchronize(c->stream);
@@ -851,16 +853,7 @@ int grid_extract_ranges(grid_ctx *c, const int32_t *C_sorted, int64_t count, int
     if (count > 0 && !C_sorted) return GRID_EINVAL;
     DeviceGuard g(c->device);
     GG_TRY(reset_ctl(c));
-    gg::ExtractArgs xa{};
-    xa.keys = (const unsigned *)C_sorted;
-    xa.count = (unsigned long long)count;
-    xa.ncells = (unsigned long long)ncells;
-    xa.G = (unsigned *)cells;
-    xa.ctl = c->d_ctl;
-    {
-        KernelScope ks(c, K_EXTRACT, 4.0 * count + 4.0 * (ncells + 1));
-        GG_CUDA(gg::launch_extract(xa, c->stream));
-    }
+    GG_TRY(extract_ranges(c, (const unsigned *)C_sorted, count, ncells, (unsigned *)cells));
     GG_TRY(read_ctl(c));
     return ctl_error(c->h_ctl->err);
 }
