@@ -278,7 +278,7 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_tris": scene.n, "lambda": scene.lam, "grid": list(info.res),
                    "ncells": info.ncells, "nrefs": nrefs, "key_bits": info.key_bits,
-                   "radix_bits": args.radix_bits or 8, "l2": "inputs larger than L2 (474 MB)",
+                   "radix_bits": args.radix_bits or 9, "l2": "inputs larger than L2 (474 MB)",
                    "parallelism": f"replicas{world}"},
         "builds_per_s": world * args.steps / (ms_max / 1e3),
         "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,

@@ -91,7 +91,7 @@ typedef struct {
 
 /* Tuning knobs; zero means "library default / autotuned". */
 typedef struct {
-    int32_t radix_bits;   /* widest digit of the LSD radix sort: 8..11 */
+    int32_t radix_bits;   /* widest digit of the LSD radix sort: 8..11 (default 9) */
     int32_t reserved[7];
 } grid_opts;
 

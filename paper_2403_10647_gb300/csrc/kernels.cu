@@ -431,124 +431,38 @@ __global__ void __launch_bounds__(BLOCK) emit_kernel(EmitArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// a8: radix sort - digit histograms of all passes
+// a8: RadixSort(C, O) - stable LSD passes, each an upsweep and a downsweep
 // ---------------------------------------------------------------------------
-
-template <int BLOCK, int ITEMS, int RBITS, int SRC>
-__global__ void __launch_bounds__(BLOCK) hist_kernel(HistArgs a)
-{
-    constexpr int T = BLOCK * ITEMS;
-    constexpr int R = 1 << RBITS;
-    extern __shared__ __align__(16) unsigned smem[];
-    unsigned *s_hist = smem;                          // [MAX_PASSES][R]
-    unsigned *s_mark = s_hist + MAX_PASSES * R;       // [padded T] (generated keys only)
-    __shared__ unsigned s_tmp[BLOCK / 32];
-    __shared__ unsigned s_last;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < a.npasses * R; i += BLOCK) s_hist[i] = 0u;
-    __syncthreads();
-
-    for (unsigned t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        const unsigned j0 = t * (unsigned)T;
-        const unsigned cnt = min((unsigned)T, a.count - j0);
-        unsigned keys[ITEMS];
-        if (SRC == SRC_GEN) {
-            unsigned objs[ITEMS];
-            const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
-            gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
-        } else {
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const unsigned e = tid * ITEMS + i;
-                keys[i] = e < cnt ? __ldg(a.keys_in + j0 + e) : 0u;
-            }
-        }
-        const unsigned nv = cnt > (unsigned)(tid * ITEMS) ? min((unsigned)ITEMS, cnt - tid * ITEMS) : 0u;
-        // the first pass's digit changes with almost every pair: one shared
-        // atomic per pair; higher digits repeat along a thread's run of
-        // consecutive pairs: one atomic per run (predicated, no branches)
-        {
-            const unsigned sh = a.shift[0], mk = (1u << a.bits[0]) - 1u;
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i)
-                if ((unsigned)i < nv) atomicAdd(&s_hist[(keys[i] >> sh) & mk], 1u);
-        }
-#pragma unroll
-        for (int p = 1; p < MAX_PASSES; ++p) {
-            if (p >= a.npasses) break;
-            const unsigned sh = a.shift[p], mk = (1u << a.bits[p]) - 1u;
-            unsigned prev = (keys[0] >> sh) & mk, run = nv ? 1u : 0u;
-#pragma unroll
-            for (int i = 1; i < ITEMS; ++i) {
-                const unsigned d = (keys[i] >> sh) & mk;
-                const bool more = (unsigned)i < nv;
-                const bool flush = more && d != prev;
-                if (flush) atomicAdd(&s_hist[p * R + prev], run);
-                run = flush ? 1u : run + (more ? 1u : 0u);
-                prev = flush ? d : prev;
-            }
-            if (run) atomicAdd(&s_hist[p * R + prev], run);
-        }
-        // this tile's look-back row of the first sort pass starts at zero
-        for (int d = tid; d < a.status_row; d += BLOCK) a.status0[(size_t)t * a.status_row + d] = 0u;
-        __syncthreads();
-    }
-    __syncthreads();
-    for (int i = tid; i < a.npasses * R; i += BLOCK) {
-        const unsigned v = s_hist[i];
-        if (v) atomicAdd(&a.hist[(i / R) * MAX_RADIX + (i % R)], v);
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&a.ctl->hist_done, 1u) == gridDim.x - 1u);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // last block: exclusive scan of every pass's histogram -> digit bases
-#pragma unroll
-    for (int p = 0; p < MAX_PASSES; ++p) {
-        if (p >= a.npasses) break;
-        const int nd = 1 << a.bits[p];
-        unsigned carry = 0;
-        for (int c0 = 0; c0 < nd; c0 += BLOCK) {
-            const int d = c0 + tid;
-            const unsigned v = d < nd ? __ldcg(&a.hist[p * MAX_RADIX + d]) : 0u;
-            unsigned tot;
-            const unsigned ex = block_excl_sum<BLOCK>(v, s_tmp, &tot);
-            if (d < nd) {
-                a.dbase[p * MAX_RADIX + d] = carry + ex;
-                a.hist[p * MAX_RADIX + d] = 0u;   // leave the histogram zeroed for the next use
-            }
-            carry += tot;
-        }
-    }
-    if (tid < MAX_PASSES) a.ctl->tickets[1 + tid] = 0u;
-    if (tid == 0) a.ctl->hist_done = 0u;
-}
-
-// ---------------------------------------------------------------------------
-// a8: radix sort - one onesweep-style LSD pass
-// ---------------------------------------------------------------------------
-
+//
+// Upsweep of pass p: per tile of PAIR_TILE pairs, the count of each digit;
+// per group of GROUP_TILES consecutive tiles, one block walks its tiles in
+// order and writes each tile's digit offsets inside the group, then a
+// decoupled look-back across groups yields each group's offsets.  Groups
+// start GROUP_TILES times less often than tiles, so look-back chains stay
+// short at GB300's tile rate.  The first pass's upsweep generates the pairs
+// (no pair array exists yet) and also counts every later pass's digits, so
+// all digit totals are known before any scatter.
+//
+// Downsweep of pass p: every tile independently ranks its elements stably
+// by digit and scatters them to dbase[d] + group offset + tile offset +
+// rank; no tile waits for another.
 
 constexpr unsigned LB_PREFIX = 0x80000000u;   // status word: value = inclusive prefix;
-                                              // else value - 1 = tile aggregate; 0 = not ready
+                                              // else value - 1 = aggregate; 0 = not ready
 
-// Decoupled look-back for one digit: sums the aggregates of the preceding
-// tiles until one that published its inclusive prefix, reading four
-// predecessors per step so long chains cost a quarter of the round trips.
-// st points at this digit's column (stride R words per tile).  Bounded: past
-// SPIN_LIMIT polls of a not-yet-published word it records ERR_TIMEOUT and
+// Decoupled look-back of group g for one digit over row-major status words
+// (st + h * R is group h's row), four predecessors per round trip.  Bounded:
+// past SPIN_LIMIT polls of an unpublished word it records ERR_TIMEOUT and
 // returns what it has.
-__device__ __forceinline__ unsigned lookback(const unsigned *st, unsigned R, unsigned tile, Ctl *ctl)
+__device__ __forceinline__ unsigned group_lookback(const unsigned *col, unsigned R, unsigned g, Ctl *ctl)
 {
     unsigned excl = 0;
-    long long k = (long long)tile - 1;
+    long long k = (long long)g - 1;
     unsigned spins = 0;
     while (k >= 0) {
         unsigned v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = k - q >= 0 ? ld_relaxed_u32(st + (size_t)(k - q) * R) : LB_PREFIX;
+        for (int q = 0; q < 4; ++q) v[q] = k - q >= 0 ? ld_relaxed_u32(col + (size_t)(k - q) * R) : LB_PREFIX;
         int used = 0;
         bool done = false;
 #pragma unroll
@@ -569,10 +483,134 @@ __device__ __forceinline__ unsigned lookback(const unsigned *st, unsigned R, uns
                 atomicOr(&ctl->err, ERR_TIMEOUT);
                 break;
             }
-            if (spins > 4) __nanosleep(32);
+            if (spins > 4) __nanosleep(64);
         }
     }
     return excl;
+}
+
+template <int BLOCK, int ITEMS, int RBITS, int SRC>
+__global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
+{
+    constexpr int T = BLOCK * ITEMS;
+    constexpr int R = 1 << RBITS;
+    extern __shared__ __align__(16) unsigned smem[];
+    unsigned *s_cnt = smem;                          // [R] this tile's digit counts
+    unsigned *s_run = s_cnt + R;                     // [R] counts of the group's tiles so far
+    unsigned *s_hist = s_run + R;                    // [MAX_PASSES][R] later passes' digits (with_hist)
+    unsigned *s_mark = s_hist + MAX_PASSES * R;      // [padded T] object marks (generated pairs)
+    __shared__ unsigned s_tmp[BLOCK / 32];
+    __shared__ unsigned s_last;
+    const int tid = threadIdx.x;
+    const unsigned g = blockIdx.x;
+    const unsigned t0 = g * GROUP_TILES, t1 = min(t0 + GROUP_TILES, a.ntiles);
+    const unsigned sh = a.shift[0], mk = (1u << a.bits[0]) - 1u;
+    for (int i = tid; i < (2 + MAX_PASSES) * R; i += BLOCK) smem[i] = 0u;
+    __syncthreads();
+
+    for (unsigned t = t0; t < t1; ++t) {
+        const unsigned j0 = t * (unsigned)T;
+        const unsigned cnt = min((unsigned)T, a.count - j0);
+        unsigned keys[ITEMS];
+        if (SRC == SRC_GEN) {
+            unsigned objs[ITEMS];
+            const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
+            gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
+        } else {
+#pragma unroll
+            for (int i = 0; i < ITEMS; i += 4) {
+                const unsigned e = tid * ITEMS + i;
+                if (e + 3 < cnt) {
+                    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(a.keys_in + j0 + e));
+                    keys[i] = v.x;
+                    keys[i + 1] = v.y;
+                    keys[i + 2] = v.z;
+                    keys[i + 3] = v.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) keys[i + q] = e + q < cnt ? a.keys_in[j0 + e + q] : 0u;
+                }
+            }
+        }
+        const unsigned nv = cnt > (unsigned)(tid * ITEMS) ? min((unsigned)ITEMS, cnt - tid * ITEMS) : 0u;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i)
+            if ((unsigned)i < nv) atomicAdd(&s_cnt[(keys[i] >> sh) & mk], 1u);
+        if (a.with_hist) {
+            // later passes' digits repeat along a thread's run of consecutive
+            // pairs: one shared atomic per run (predicated, no branches)
+#pragma unroll
+            for (int p = 1; p < MAX_PASSES; ++p) {
+                if (p >= a.npasses) break;
+                const unsigned shp = a.shift[p], mkp = (1u << a.bits[p]) - 1u;
+                unsigned prev = (keys[0] >> shp) & mkp, run = nv ? 1u : 0u;
+#pragma unroll
+                for (int i = 1; i < ITEMS; ++i) {
+                    const unsigned d = (keys[i] >> shp) & mkp;
+                    const bool more = (unsigned)i < nv;
+                    const bool flush = more && d != prev;
+                    if (flush) atomicAdd(&s_hist[p * R + prev], run);
+                    run = flush ? 1u : run + (more ? 1u : 0u);
+                    prev = flush ? d : prev;
+                }
+                if (run) atomicAdd(&s_hist[p * R + prev], run);
+            }
+        }
+        __syncthreads();
+        for (int d = tid; d < R; d += BLOCK) {
+            a.intra[(size_t)t * R + d] = s_run[d];
+            s_run[d] += s_cnt[d];
+            s_cnt[d] = 0u;
+        }
+        __syncthreads();
+    }
+
+    // the group's offsets: decoupled look-back across groups, per digit
+    for (int d = tid; d < R; d += BLOCK) {
+        const unsigned tot = s_run[d];
+        unsigned *col = a.status + d;
+        unsigned excl = 0;
+        if (g == 0) {
+            st_relaxed_u32(col, LB_PREFIX | tot);
+        } else {
+            st_relaxed_u32(col + (size_t)g * R, tot + 1u);
+            excl = group_lookback(col, R, g, a.ctl);
+            st_relaxed_u32(col + (size_t)g * R, LB_PREFIX | (excl + tot));
+        }
+        a.gpref[(size_t)g * R + d] = excl;
+    }
+    if (!a.with_hist) return;
+
+    // digit totals of every pass -> exclusive digit starts (last block)
+    __syncthreads();
+    for (int i = tid; i < a.npasses * R; i += BLOCK) {
+        const unsigned v = i < R ? s_run[i] : s_hist[i];
+        if (v) atomicAdd(&a.hist[(i / R) * MAX_RADIX + (i % R)], v);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&a.ctl->hist_done, 1u) == gridDim.x - 1u);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int p = 0; p < MAX_PASSES; ++p) {
+        if (p >= a.npasses) break;
+        const int nd = 1 << a.bits[p];
+        unsigned carry = 0;
+        for (int c0 = 0; c0 < nd; c0 += BLOCK) {
+            const int d = c0 + tid;
+            const unsigned v = d < nd ? __ldcg(&a.hist[p * MAX_RADIX + d]) : 0u;
+            unsigned tot;
+            const unsigned ex = block_excl_sum<BLOCK>(v, s_tmp, &tot);
+            if (d < nd) {
+                a.dbase[p * MAX_RADIX + d] = carry + ex;
+                a.hist[p * MAX_RADIX + d] = 0u;   // leave the histogram zeroed for the next use
+            }
+            carry += tot;
+        }
+    }
+    if (tid == 0) a.ctl->hist_done = 0u;
 }
 
 // Shared-memory index for 64-bit elements: one pad element per 16, so blocked
@@ -582,11 +620,31 @@ __device__ __forceinline__ unsigned pad16(unsigned e) { return e + (e >> 4); }
 template <int T>
 __host__ __device__ constexpr int padded16() { return T + T / 16; }
 
+// The peer masks of the ranking step live inside the staging buffer, which
+// is idle while a tile is being ranked: items go through the ranking steps
+// in batches of 4, 2 or 1, the largest whose masks fit there (0: even one
+// batch does not fit, and four separate mask buffers follow the counts).
 template <int BLOCK, int ITEMS, int RBITS>
-constexpr size_t pass_smem_bytes()
+__host__ __device__ constexpr int mask_batch()
+{
+    return (4 * (BLOCK / 32) * (1 << RBITS) * 4 <= padded16<BLOCK * ITEMS>() * 8)   ? 4
+           : (2 * (BLOCK / 32) * (1 << RBITS) * 4 <= padded16<BLOCK * ITEMS>() * 8) ? 2
+           : ((BLOCK / 32) * (1 << RBITS) * 4 <= padded16<BLOCK * ITEMS>() * 8)     ? 1
+                                                                                     : 0;
+}
+
+template <int BLOCK, int ITEMS, int RBITS>
+__host__ __device__ constexpr bool masks_in_stage()
+{
+    return mask_batch<BLOCK, ITEMS, RBITS>() > 0;
+}
+
+template <int BLOCK, int ITEMS, int RBITS>
+__host__ __device__ constexpr size_t down_smem_bytes()
 {
     return sizeof(unsigned long long) * padded16<BLOCK * ITEMS>() +
-           sizeof(unsigned) * (4 * (BLOCK / 32) * (1 << RBITS) + ((1 << RBITS) + 1) + (1 << RBITS) + BLOCK / 32 + 4);
+           sizeof(unsigned) * ((masks_in_stage<BLOCK, ITEMS, RBITS>() ? 1 : 5) * (BLOCK / 32) * (1 << RBITS) +
+                               2 * (1 << RBITS) + BLOCK / 32);
 }
 
 __device__ __forceinline__ unsigned long long pack_kv(unsigned k, unsigned v)
@@ -594,8 +652,8 @@ __device__ __forceinline__ unsigned long long pack_kv(unsigned k, unsigned v)
     return ((unsigned long long)k << 32) | v;
 }
 
-template <int BLOCK, int ITEMS, int RBITS, int IN, int OUT>
-__global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) pass_kernel(PassArgs a)
+template <int BLOCK, int ITEMS, int RBITS, int IN>
+__global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownArgs a)
 {
     constexpr int W = BLOCK / 32;
     constexpr int T = BLOCK * ITEMS;
@@ -603,91 +661,113 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) pass_kernel(PassArgs a
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long *s_elem = reinterpret_cast<unsigned long long *>(smem_raw);   // [padded16 T]
     unsigned *s_mark = reinterpret_cast<unsigned *>(smem_raw);   // object marks while generating (aliases s_elem)
+    constexpr bool ALIAS = masks_in_stage<BLOCK, ITEMS, RBITS>();
     unsigned *s_whist = reinterpret_cast<unsigned *>(s_elem + padded16<T>());      // [W][R] warp digit counts
-    unsigned *s_wmask = s_whist + W * R;        // [3][W][R] peer masks, three rotating buffers
-    unsigned *s_dstart = s_wmask + 3 * W * R;   // [R + 1]
-    unsigned *s_gbase = s_dstart + R + 1;       // [R]
+    constexpr int BATCH = ALIAS ? mask_batch<BLOCK, ITEMS, RBITS>() : 4;
+    unsigned *s_wmask = ALIAS ? reinterpret_cast<unsigned *>(smem_raw) : s_whist + W * R;   // [BATCH][W][R] peer masks
+    unsigned *s_dstart = s_whist + (ALIAS ? 1 : 5) * W * R;   // [R]
+    unsigned *s_gbase = s_dstart + R;           // [R]
     unsigned *s_tmp = s_gbase + R;              // [W]
-    unsigned *s_misc = s_tmp + W;               // [4]
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (tid == 0) s_misc[0] = atomicAdd(a.ticket, 1u);
-    for (int i = tid; i < 4 * W * R; i += BLOCK) s_whist[i] = 0u;
-    __syncthreads();
-    const unsigned tile = s_misc[0];
+    const unsigned tile = blockIdx.x;
+    const unsigned group = tile / GROUP_TILES;
+    const unsigned nd = 1u << a.bits;
+    for (int i = tid; i < W * R; i += BLOCK) s_whist[i] = 0u;
+    if (!ALIAS || IN != IN_GEN)   // generated tiles pass through the staging buffer first
+        for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
+    for (int d = tid; d < R; d += BLOCK)
+        s_gbase[d] = d < (int)nd ? __ldg(a.dbase + d) + __ldg(a.gpref + (size_t)group * R + d) +
+                                       __ldg(a.intra + (size_t)tile * R + d)
+                                 : 0u;
     const unsigned j0 = tile * (unsigned)T;
     const unsigned cnt = min((unsigned)T, a.count - j0);
-    const unsigned sh = a.shift, mk = (1u << a.bits) - 1u;
+    const unsigned sh = a.shift, mk = nd - 1u;
 
     // element of item i for this lane (warp-striped): e = w * 32 * ITEMS + i * 32 + lane
-    unsigned long long el[ITEMS];
+    unsigned keys[ITEMS], vals[ITEMS];
     if (IN == IN_GEN) {
-        unsigned keys[ITEMS], objs[ITEMS];
+        __syncthreads();
         const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, tile, j0, cnt, s_mark, s_tmp);
-        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
+        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, vals);
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) s_elem[pad16(tid * ITEMS + i)] = pack_kv(keys[i], objs[i]);
+        for (int i = 0; i < ITEMS; ++i) s_elem[pad16(tid * ITEMS + i)] = pack_kv(keys[i], vals[i]);
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i) el[i] = s_elem[pad16(w * 32 * ITEMS + i * 32 + lane)];
-    } else if (IN == IN_PAIR) {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-            const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-            el[i] = e < cnt ? pack_kv(__ldcs(a.keys_in + j0 + e), __ldcs(a.vals_in + j0 + e)) : 0ull;
+            const unsigned long long v = s_elem[pad16(w * 32 * ITEMS + i * 32 + lane)];
+            keys[i] = (unsigned)(v >> 32);
+            vals[i] = (unsigned)v;
+        }
+        if (ALIAS) {
+            __syncthreads();   // the staging buffer is read out; the masks may take it
+            for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
         }
     } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-            el[i] = e < cnt ? __ldcs(a.elems_in + j0 + e) : 0ull;
+            keys[i] = e < cnt ? __ldcs(a.keys_in + j0 + e) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const unsigned e = w * 32 * ITEMS + i * 32 + lane;
+            vals[i] = e < cnt ? __ldcs(a.vals_in + j0 + e) : 0u;
         }
     }
+    __syncthreads();
 
     // warp-level multisplit, stable in element order (items in order, lanes in
     // order): the lanes holding digit d find each other by OR-ing their lane
     // bit into a shared mask word for d; the lowest of them reserves the
     // group's slots in the warp's digit count with one shared atomic and the
-    // old count is broadcast.  Three mask buffers rotate so a buffer is
-    // cleared one item after its use and reused one item later, with a single
-    // warp barrier per item.
-    static_assert(ITEMS % 2 == 0 && T <= 65536, "ranks are packed in 16-bit pairs");
+    // old count is broadcast.  BATCH items go through each step together so
+    // their shared-memory round trips overlap; the reservations are issued in
+    // item order, which keeps the ranks stable.
+    static_assert(ITEMS % 2 == 0 && ITEMS % BATCH == 0 && T <= 65536, "ranks are packed in 16-bit pairs");
     unsigned ranks[ITEMS / 2];   // 16-bit ranks, two per register
     unsigned *wh = s_whist + w * R;
     const unsigned ltmask = lanemask_lt();
     const unsigned bit = 1u << lane;
-    unsigned clear_d = 0u;
-    bool clear_me = false;
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-        const bool ok = e < cnt;
-        const unsigned d = (unsigned)(el[i] >> 32 >> sh) & mk;
-        unsigned *wm = s_wmask + (i % 3) * W * R + w * R;
-        if (ok) atomicOr(&wm[d], bit);
+    for (int ib = 0; ib < ITEMS; ib += BATCH) {
+        unsigned d[BATCH], peers[BATCH], old[BATCH];
+        bool ok[BATCH];
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+            const unsigned e = w * 32 * ITEMS + (ib + q) * 32 + lane;
+            ok[q] = e < cnt;
+            d[q] = (keys[ib + q] >> sh) & mk;
+            if (ok[q]) atomicOr(&s_wmask[(q * W + w) * R + d[q]], bit);
+        }
         __syncwarp();
-        if (clear_me) s_wmask[((i + 2) % 3) * W * R + w * R + clear_d] = 0u;   // previous item's word
-        const unsigned peers = ok ? wm[d] : 0u;
-        const unsigned lt = __popc(peers & ltmask);
-        const bool leader = ok && lt == 0u;
-        unsigned old = 0u;
-        if (leader) old = atomicAdd(&wh[d], __popc(peers));
-        old = __shfl_sync(0xffffffffu, old, ok ? __ffs(peers) - 1 : lane);
-        if (i % 2 == 0)
-            ranks[i / 2] = old + lt;
-        else
-            ranks[i / 2] |= (old + lt) << 16;
-        clear_me = leader;
-        clear_d = d;
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) peers[q] = ok[q] ? s_wmask[(q * W + w) * R + d[q]] : 0u;
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+            old[q] = 0u;
+            if (ok[q] && (peers[q] & ltmask) == 0u) {
+                old[q] = atomicAdd(&wh[d[q]], __popc(peers[q]));
+                s_wmask[(q * W + w) * R + d[q]] = 0u;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+            const unsigned r = __shfl_sync(0xffffffffu, old[q], ok[q] ? __ffs(peers[q]) - 1 : lane) +
+                               __popc(peers[q] & ltmask);
+            const int i = ib + q;
+            if (i % 2 == 0)
+                ranks[i / 2] = r;
+            else
+                ranks[i / 2] |= r << 16;
+        }
     }
-    __syncwarp();
-    if (clear_me) s_wmask[((ITEMS + 2) % 3) * W * R + w * R + clear_d] = 0u;
     __syncthreads();
 
-    // per digit: exclusive offsets across warps and the tile's count; the
-    // aggregate is published and the look-back run at once, so the inclusive
-    // prefix reaches the following tiles as early as possible
+    // per digit: exclusive offsets across warps and the tile's count
     for (int d = tid; d < R; d += BLOCK) {
         unsigned sum = 0;
 #pragma unroll
@@ -696,18 +776,7 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) pass_kernel(PassArgs a
             s_whist[ww * R + d] = sum;
             sum += c;
         }
-        unsigned *st = a.status + (size_t)tile * R + d;
-        unsigned excl = 0;
-        if (tile == 0) {
-            st_relaxed_u32(st, LB_PREFIX | sum);
-        } else {
-            st_relaxed_u32(st, sum + 1u);
-            excl = lookback(a.status + d, R, tile, a.ctl);
-            st_relaxed_u32(st, LB_PREFIX | (excl + sum));
-        }
         s_dstart[d] = sum;
-        s_gbase[d] = a.dbase[d] + excl;
-        if (a.status_next) a.status_next[(size_t)tile * R + d] = 0u;
     }
     __syncthreads();
     // exclusive scan of the tile's digit counts -> local digit starts
@@ -732,14 +801,17 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) pass_kernel(PassArgs a
         }
     }
     __syncthreads();
+    // each warp's slot base per digit: local digit start + earlier warps' share
+    for (int i = tid; i < W * R; i += BLOCK) s_whist[i] += s_dstart[i % R];
+    __syncthreads();
     // stage the tile in shared memory in locally sorted order
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const unsigned e = w * 32 * ITEMS + i * 32 + lane;
         if (e < cnt) {
-            const unsigned d = (unsigned)(el[i] >> 32 >> sh) & mk;
+            const unsigned d = (keys[i] >> sh) & mk;
             const unsigned rk = (ranks[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
-            s_elem[s_dstart[d] + s_whist[w * R + d] + rk] = el[i];
+            s_elem[s_whist[w * R + d] + rk] = pack_kv(keys[i], vals[i]);
         }
     }
     __syncthreads();
@@ -750,14 +822,11 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) pass_kernel(PassArgs a
         const unsigned pos = i * BLOCK + tid;
         if (pos < cnt) {
             const unsigned long long v = s_elem[pos];
-            const unsigned dst = s_gbase[(unsigned)(v >> 32 >> sh) & mk] + pos;
+            const unsigned k = (unsigned)(v >> 32);
+            const unsigned dst = s_gbase[(k >> sh) & mk] + pos;
             if (dst < a.count) {
-                if (OUT == OUT_PACKED) {
-                    __stcg(a.elems_out + dst, v);
-                } else {
-                    __stcg(a.keys_out + dst, (unsigned)(v >> 32));
-                    __stcg(a.vals_out + dst, (unsigned)v);
-                }
+                __stcg(a.keys_out + dst, k);
+                __stcg(a.vals_out + dst, (unsigned)v);
             } else {
                 bad = true;
             }
@@ -767,7 +836,7 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) pass_kernel(PassArgs a
 }
 
 // ---------------------------------------------------------------------------
-// a9: RunLengthEncode + NonEmptyCells + ExclusiveSum as one merge path
+// a9: RunLengthEncode + NonEmptyCells + ExclusiveSum via a merge path
 // ---------------------------------------------------------------------------
 
 // Merge order: cell c precedes key k iff c <= k, so G[c] = number of keys
@@ -797,6 +866,8 @@ __global__ void __launch_bounds__(256) extract_split_kernel(ExtractArgs a, unsig
     const unsigned long long nA = a.count, nB = a.ncells + 1ull;
     const unsigned long long d = min(b * (unsigned long long)EXTRACT_TILE, nA + nB);
     a.splits[b] = (unsigned)merge_split(a.keys, nA, nB, d);
+    // the keys are sorted: the last one bounds them all
+    if (b == 0 && nA > 0 && (unsigned long long)__ldg(a.keys + nA - 1) >= a.ncells) atomicOr(&a.ctl->err, ERR_RANGE);
 }
 
 template <int BLOCK, int ITEMS>
@@ -804,7 +875,6 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
 {
     constexpr int D = BLOCK * ITEMS;
     __shared__ unsigned s_keys[D];
-    __shared__ unsigned s_G[D];
     const int tid = threadIdx.x;
     const unsigned long long nA = a.count, nB = a.ncells + 1ull;
     const unsigned long long M = nA + nB;
@@ -812,39 +882,25 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
     const unsigned long long d1 = min(d0 + D, M);
     const unsigned long long i0 = a.splits[blockIdx.x], i1 = a.splits[blockIdx.x + 1];
     const unsigned long long c0 = d0 - i0, c1 = d1 - i1;
-    const unsigned na = (unsigned)(i1 - i0), nb = (unsigned)(c1 - c0);
+    const unsigned na = (unsigned)(i1 - i0);
     for (unsigned k = tid; k < na; k += BLOCK) s_keys[k] = __ldcs(a.keys + i0 + k);
     __syncthreads();
-    const unsigned td0 = tid * ITEMS;
-    const unsigned nd = (unsigned)(d1 - d0);
-    if (td0 < nd) {
-        // local split on the diagonal td0 of (s_keys[0..na), cells c0 ..)
-        unsigned lo = td0 > nb ? td0 - nb : 0u;
-        unsigned hi = min(td0, na);
-        while (lo < hi) {
-            const unsigned mid = (lo + hi) >> 1;
-            if ((unsigned long long)s_keys[mid] < c0 + (td0 - mid - 1u))
-                lo = mid + 1u;
-            else
-                hi = mid;
-        }
-        unsigned ia = lo, ib = td0 - lo;
-        const unsigned steps = min((unsigned)ITEMS, nd - td0);
-        unsigned bad = 0;
-        for (unsigned s = 0; s < steps; ++s) {
-            const bool take_cell = ib < nb && (ia >= na || c0 + ib <= (unsigned long long)s_keys[ia]);
-            if (take_cell) {
-                s_G[ib] = (unsigned)(i0 + ia);
-                ++ib;
+    // every key before i0 is below c0 and every key from i1 on is at least
+    // c1, so G[c] = i0 + (keys of this block below c): one lower-bound search
+    // in shared memory per cell, consecutive threads on consecutive cells
+    for (unsigned long long c = c0 + tid; c < c1; c += BLOCK) {
+        unsigned lo = 0, len = na;
+        while (len > 0) {
+            const unsigned half = len >> 1;
+            if ((unsigned long long)s_keys[lo + half] < c) {
+                lo += half + 1u;
+                len -= half + 1u;
             } else {
-                if (ia < na && s_keys[ia] >= a.ncells) bad = 1u;
-                ++ia;
+                len = half;
             }
         }
-        if (bad) atomicOr(&a.ctl->err, ERR_RANGE);
+        a.G[c] = (unsigned)(i0 + lo);
     }
-    __syncthreads();
-    for (unsigned k = tid; k < nb; k += BLOCK) a.G[c0 + k] = s_G[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -895,31 +951,28 @@ cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s)
 }
 
 template <int RBITS, int SRC>
-static cudaError_t launch_hist_t(const HistArgs &a, int nsm, cudaStream_t s)
+static cudaError_t launch_up_t(const UpArgs &a, cudaStream_t s)
 {
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
-    auto k = hist_kernel<PAIR_BLOCK, ITEMS, RBITS, SRC>;
-    const size_t smem = sizeof(unsigned) * (MAX_PASSES * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
+    auto k = upsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, SRC>;
+    const size_t smem = sizeof(unsigned) * ((2 + MAX_PASSES) * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    unsigned blocks = a.ntiles;
-    const unsigned cap = (unsigned)nsm * 4u;
-    if (blocks > cap) blocks = cap;
-    if (blocks == 0) blocks = 1;
-    k<<<blocks, PAIR_BLOCK, smem, s>>>(a);
+    const unsigned groups = (a.ntiles + GROUP_TILES - 1) / GROUP_TILES;
+    k<<<groups, PAIR_BLOCK, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int RBITS, int IN, int OUT>
-static cudaError_t launch_pass_t(const PassArgs &a, unsigned ntiles, cudaStream_t s)
+template <int RBITS, int IN>
+static cudaError_t launch_down_t(const DownArgs &a, unsigned ntiles, cudaStream_t s)
 {
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
-    auto k = pass_kernel<PAIR_BLOCK, ITEMS, RBITS, IN, OUT>;
-    constexpr size_t smem = pass_smem_bytes<PAIR_BLOCK, ITEMS, RBITS>();
+    auto k = downsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, IN>;
+    constexpr size_t smem = down_smem_bytes<PAIR_BLOCK, ITEMS, RBITS>();
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -930,45 +983,38 @@ static cudaError_t launch_pass_t(const PassArgs &a, unsigned ntiles, cudaStream_
     return cudaGetLastError();
 }
 
-template <int RBITS>
-static cudaError_t launch_pass_r(const PassArgs &a, int in, int out, unsigned ntiles, cudaStream_t s)
-{
-    if (in == IN_GEN) return out == OUT_PACKED ? launch_pass_t<RBITS, IN_GEN, OUT_PACKED>(a, ntiles, s)
-                                               : launch_pass_t<RBITS, IN_GEN, OUT_PAIR>(a, ntiles, s);
-    if (in == IN_PAIR) return out == OUT_PACKED ? launch_pass_t<RBITS, IN_PAIR, OUT_PACKED>(a, ntiles, s)
-                                                : launch_pass_t<RBITS, IN_PAIR, OUT_PAIR>(a, ntiles, s);
-    return out == OUT_PACKED ? launch_pass_t<RBITS, IN_PACKED, OUT_PACKED>(a, ntiles, s)
-                             : launch_pass_t<RBITS, IN_PACKED, OUT_PAIR>(a, ntiles, s);
-}
-
-cudaError_t launch_hist(const HistArgs &a, int rbits, int src, int nsm, cudaStream_t s)
+cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s)
 {
     if (a.ntiles == 0) return cudaSuccess;
-#define GG_HIST(RB)                                                        \
+#define GG_UP(RB)                                                          \
     case RB:                                                               \
-        return src == SRC_GEN ? launch_hist_t<RB, SRC_GEN>(a, nsm, s)     \
-                              : launch_hist_t<RB, SRC_MEM>(a, nsm, s);
+        return src == SRC_GEN ? launch_up_t<RB, SRC_GEN>(a, s) : launch_up_t<RB, SRC_MEM>(a, s);
     switch (rbits) {
-        GG_HIST(8)
-        GG_HIST(9)
-        GG_HIST(10)
-        GG_HIST(11)
+        GG_UP(8)
+        GG_UP(9)
+        GG_UP(10)
+        GG_UP(11)
     default:
         return cudaErrorInvalidValue;
     }
-#undef GG_HIST
+#undef GG_UP
 }
 
-cudaError_t launch_pass(const PassArgs &a, int rbits, int in, int out, unsigned ntiles, cudaStream_t s)
+cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, cudaStream_t s)
 {
     if (ntiles == 0) return cudaSuccess;
+#define GG_DOWN(RB)                                                        \
+    case RB:                                                               \
+        return in == IN_GEN ? launch_down_t<RB, IN_GEN>(a, ntiles, s) : launch_down_t<RB, IN_PAIR>(a, ntiles, s);
     switch (rbits) {
-    case 8: return launch_pass_r<8>(a, in, out, ntiles, s);
-    case 9: return launch_pass_r<9>(a, in, out, ntiles, s);
-    case 10: return launch_pass_r<10>(a, in, out, ntiles, s);
-    case 11: return launch_pass_r<11>(a, in, out, ntiles, s);
-    default: return cudaErrorInvalidValue;
+        GG_DOWN(8)
+        GG_DOWN(9)
+        GG_DOWN(10)
+        GG_DOWN(11)
+    default:
+        return cudaErrorInvalidValue;
     }
+#undef GG_DOWN
 }
 
 unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells)

@@ -19,11 +19,15 @@ namespace gg {
 #ifndef GG_PASS_MIN_BLOCKS
 #define GG_PASS_MIN_BLOCKS 3
 #endif
+#ifndef GG_GROUP_TILES
+#define GG_GROUP_TILES 16
+#endif
 constexpr int COUNT_BLOCK = 256;
 constexpr int COUNT_TILE = 2048;
 constexpr int PAIR_BLOCK = GG_PAIR_BLOCK;
 constexpr int PAIR_TILE = GG_PAIR_BLOCK * GG_PAIR_ITEMS;
 constexpr int PASS_MIN_BLOCKS = GG_PASS_MIN_BLOCKS;
+constexpr int GROUP_TILES = GG_GROUP_TILES;   // tiles per upsweep block
 constexpr int EXTRACT_BLOCK = 256;
 constexpr int EXTRACT_TILE = 2048;
 
@@ -51,46 +55,45 @@ struct EmitArgs {
     unsigned *O;
 };
 
-struct HistArgs {
+// Upsweep of one radix-sort pass: digit counts per tile, offsets of each
+// tile inside its group of GROUP_TILES tiles, offsets of each group.  With
+// with_hist it also counts the digits of every pass and writes the digit
+// starts (dbase) of all passes.
+struct UpArgs {
     const unsigned *keys_in;        // SRC_MEM
     const ObjRec *recs;             // SRC_GEN
     const unsigned *tile_obj;       // SRC_GEN
     unsigned res_x, res_y;          // SRC_GEN
     unsigned count;
     unsigned ntiles;
-    int npasses;
+    int npasses;                    // with_hist: passes counted; shift[0]/bits[0] = this pass
     int shift[MAX_PASSES];
     int bits[MAX_PASSES];
-    unsigned *hist;                 // [MAX_PASSES][MAX_RADIX], zero on entry, zero on exit
-    unsigned *dbase;                // [MAX_PASSES][MAX_RADIX] out: exclusive digit starts
-    unsigned *status0;              // [ntiles][status_row] zeroed here for the first pass
-    int status_row;
+    int with_hist;
+    unsigned *intra;                // [ntiles][2^RBITS] out: tile offsets inside its group
+    unsigned *gpref;                // [ngroups][2^RBITS] out: group offsets
+    unsigned *status;               // [ngroups][2^RBITS] look-back words, zero on entry
+    unsigned *hist;                 // [MAX_PASSES][MAX_RADIX], zero on entry and exit (with_hist)
+    unsigned *dbase;                // [MAX_PASSES][MAX_RADIX] out (with_hist)
     Ctl *ctl;
 };
 
-// Element layouts of a radix-sort pass.  Between passes an element travels
-// as one 64-bit word (key << 32 | value); the first pass may instead read two
-// int32 arrays or generate the object-order pairs itself, the last may write
-// two arrays.
-enum { IN_GEN = 0, IN_PAIR = 1, IN_PACKED = 2 };
-enum { OUT_PACKED = 0, OUT_PAIR = 1 };
+// Downsweep of one pass: stable rank and scatter of each tile.
+enum { IN_GEN = 0, IN_PAIR = 1 };
 
-struct PassArgs {
+struct DownArgs {
     const unsigned *keys_in;        // IN_PAIR
     const unsigned *vals_in;        // IN_PAIR
-    const unsigned long long *elems_in;   // IN_PACKED
     const ObjRec *recs;             // IN_GEN
     const unsigned *tile_obj;       // IN_GEN
     unsigned res_x, res_y;          // IN_GEN
-    unsigned long long *elems_out;  // OUT_PACKED
-    unsigned *keys_out;             // OUT_PAIR
-    unsigned *vals_out;             // OUT_PAIR
+    unsigned *keys_out;
+    unsigned *vals_out;
     unsigned count;
     int shift, bits;
-    const unsigned *dbase;          // [2^bits] global digit starts of this pass
-    unsigned *status;               // [ntiles][2^RBITS] zero on entry
-    unsigned *status_next;          // zeroed here for the next pass (nullable)
-    unsigned *ticket;               // zero on entry
+    const unsigned *dbase;          // [2^bits] digit starts of this pass
+    const unsigned *gpref;          // from the upsweep
+    const unsigned *intra;          // from the upsweep
     Ctl *ctl;
 };
 
@@ -109,8 +112,8 @@ cudaError_t launch_count_scan(const CountArgs &a, cudaStream_t s);
 cudaError_t launch_tile_search(const ObjRec *recs, long long n, unsigned tile, unsigned ntiles,
                                unsigned *tile_obj, cudaStream_t s);
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s);
-cudaError_t launch_hist(const HistArgs &a, int rbits, int src, int nsm, cudaStream_t s);
-cudaError_t launch_pass(const PassArgs &a, int rbits, int in, int out, unsigned ntiles, cudaStream_t s);
+cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s);
+cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, cudaStream_t s);
 unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells);
 cudaError_t launch_extract_split(const ExtractArgs &a, cudaStream_t s);
 cudaError_t launch_extract(const ExtractArgs &a, cudaStream_t s);

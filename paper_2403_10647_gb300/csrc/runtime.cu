@@ -43,9 +43,11 @@ struct Scratch {
     size_t bytes = 0;
 };
 
-enum KernelId { K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_HIST, K_PASS_GEN, K_PASS, K_SPLIT, K_EXTRACT, K_NUM };
-const char *const kKernelNames[K_NUM] = {"bounds", "count_scan", "tile_search", "emit", "hist",
-                                         "pass_gen", "pass", "extract_split", "extract"};
+enum KernelId {
+    K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_NUM
+};
+const char *const kKernelNames[K_NUM] = {"bounds", "count_scan", "tile_search", "emit", "upsweep_gen",
+                                         "downsweep_gen", "upsweep", "downsweep", "extract_split", "extract"};
 
 struct PendingTiming {
     int kid;
@@ -61,14 +63,14 @@ struct grid_ctx {
     cudaStream_t stream = nullptr;
     cudaMemPool_t pool = nullptr;
     grid_opts opts{};
-    int rbits_max = 8;
+    int rbits_max = 9;
 
     Ctl *d_ctl = nullptr;        // device control block
     Ctl *h_ctl = nullptr;        // pinned host mirror
     unsigned *d_hist = nullptr;  // [MAX_PASSES][MAX_RADIX], kept zero between uses
     unsigned *d_dbase = nullptr; // [MAX_PASSES][MAX_RADIX]
 
-    Scratch recs, k2status, tile_obj, keys_sorted, packed[2], status[2], splits;
+    Scratch recs, k2status, tile_obj, keys_sorted, keys[1], vals[1], intra, gpref, gstatus, splits;
     Scratch in_verts, in_tris, out_cells, out_refs;  // host-buffer builds
     std::atomic<int64_t> in_use{0};
 
@@ -298,72 +300,79 @@ unsigned pair_tiles(int64_t count) { return (unsigned)((count + gg::PAIR_TILE - 
 
 // Radix sort of (keys, vals) over the configured passes.  If gen is set, the
 // first pass generates the object-order pairs from recs/tile_obj; otherwise
-// it reads keys_in/vals_in.  The last pass writes keys_last / vals_last.
-// Returns the buffer holding the sorted keys.
+// it reads keys_in/vals_in.  The last pass writes keys_last / vals_last;
+// pass outputs alternate between those and one scratch pair of arrays so
+// the last lands there.
 int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const ObjRec *recs, int64_t nobj,
                const unsigned *tile_obj, unsigned res_x, unsigned res_y, const unsigned *keys_in,
                const unsigned *vals_in, unsigned *keys_last, unsigned *vals_last)
 {
     const unsigned ntiles = pair_tiles(count);
+    const unsigned ngroups = (ntiles + gg::GROUP_TILES - 1) / gg::GROUP_TILES;
     const int R = 1 << sc.rbits;
-    const size_t packed_bytes = (size_t)count * sizeof(unsigned long long);
-    GG_TRY(ensure(c, c->status[0], (size_t)ntiles * R * sizeof(unsigned)));
+    const size_t elem = (size_t)count * sizeof(unsigned);
+    GG_TRY(ensure(c, c->intra, (size_t)ntiles * R * sizeof(unsigned)));
+    GG_TRY(ensure(c, c->gpref, (size_t)ngroups * R * sizeof(unsigned)));
+    GG_TRY(ensure(c, c->gstatus, (size_t)ngroups * R * sizeof(unsigned)));
     if (sc.passes > 1) {
-        GG_TRY(ensure(c, c->status[1], (size_t)ntiles * R * sizeof(unsigned)));
-        GG_TRY(ensure(c, c->packed[0], packed_bytes));
+        GG_TRY(ensure(c, c->keys[0], elem));
+        GG_TRY(ensure(c, c->vals[0], elem));
     }
-    if (sc.passes > 2) GG_TRY(ensure(c, c->packed[1], packed_bytes));
-    gg::HistArgs h{};
-    h.keys_in = keys_in;
-    h.recs = recs;
-    h.tile_obj = tile_obj;
-    h.res_x = res_x;
-    h.res_y = res_y;
-    h.count = count;
-    h.ntiles = ntiles;
-    h.npasses = sc.passes;
-    for (int p = 0; p < gg::MAX_PASSES; ++p) {
-        h.shift[p] = sc.shift[p];
-        h.bits[p] = sc.bits[p];
-    }
-    h.hist = c->d_hist;
-    h.dbase = c->d_dbase;
-    h.status0 = (unsigned *)c->status[0].ptr;
-    h.status_row = R;
-    h.ctl = c->d_ctl;
-    {
-        KernelScope ks(c, K_HIST, gen ? 16.0 * nobj : 4.0 * count);
-        GG_CUDA(gg::launch_hist(h, sc.rbits, gen ? gg::SRC_GEN : gg::SRC_MEM, c->nsm, c->stream));
-    }
-
-    // pass p reads packed[(p - 1) % 2] and writes packed[p % 2]; the first
-    // pass generates or reads two arrays, the last writes two arrays
+    unsigned *ko[gg::MAX_PASSES], *vo[gg::MAX_PASSES];
     for (int p = 0; p < sc.passes; ++p) {
-        gg::PassArgs a{};
-        const bool last = p == sc.passes - 1;
-        const int in = p > 0 ? gg::IN_PACKED : (gen ? gg::IN_GEN : gg::IN_PAIR);
-        const int out = last ? gg::OUT_PAIR : gg::OUT_PACKED;
-        a.keys_in = keys_in;
-        a.vals_in = vals_in;
-        if (p > 0) a.elems_in = (const unsigned long long *)c->packed[(p - 1) % 2].ptr;
+        const bool to_last = ((sc.passes - 1 - p) % 2) == 0;
+        ko[p] = to_last ? keys_last : (unsigned *)c->keys[0].ptr;
+        vo[p] = to_last ? vals_last : (unsigned *)c->vals[0].ptr;
+    }
+    for (int p = 0; p < sc.passes; ++p) {
+        const bool first = p == 0;
+        const unsigned *kin = first ? keys_in : ko[p - 1];
+        const unsigned *vin = first ? vals_in : vo[p - 1];
+        GG_CUDA(cudaMemsetAsync(c->gstatus.ptr, 0, (size_t)ngroups * R * sizeof(unsigned), c->stream));
+        gg::UpArgs u{};
+        u.keys_in = kin;
+        u.recs = recs;
+        u.tile_obj = tile_obj;
+        u.res_x = res_x;
+        u.res_y = res_y;
+        u.count = count;
+        u.ntiles = ntiles;
+        u.with_hist = first ? 1 : 0;
+        u.npasses = first ? sc.passes : 1;
+        for (int q = 0; q < gg::MAX_PASSES; ++q) {
+            const int pq = first ? q : p;   // with_hist: every pass's digit; else this pass's
+            u.shift[q] = sc.shift[pq < gg::MAX_PASSES ? pq : 0];
+            u.bits[q] = sc.bits[pq < gg::MAX_PASSES ? pq : 0];
+        }
+        u.intra = (unsigned *)c->intra.ptr;
+        u.gpref = (unsigned *)c->gpref.ptr;
+        u.status = (unsigned *)c->gstatus.ptr;
+        u.hist = c->d_hist;
+        u.dbase = c->d_dbase;
+        u.ctl = c->d_ctl;
+        const bool gen_up = first && gen;
+        {
+            KernelScope ks(c, gen_up ? K_UP_GEN : K_UP, gen_up ? 16.0 * nobj : 4.0 * count);
+            GG_CUDA(gg::launch_upsweep(u, sc.rbits, gen_up ? gg::SRC_GEN : gg::SRC_MEM, c->stream));
+        }
+        gg::DownArgs a{};
+        a.keys_in = kin;
+        a.vals_in = vin;
         a.recs = recs;
         a.tile_obj = tile_obj;
         a.res_x = res_x;
         a.res_y = res_y;
-        if (!last) a.elems_out = (unsigned long long *)c->packed[p % 2].ptr;
-        a.keys_out = keys_last;
-        a.vals_out = vals_last;
+        a.keys_out = ko[p];
+        a.vals_out = vo[p];
         a.count = count;
         a.shift = sc.shift[p];
         a.bits = sc.bits[p];
         a.dbase = c->d_dbase + p * gg::MAX_RADIX;
-        a.status = (unsigned *)c->status[p % 2].ptr;
-        a.status_next = p + 1 < sc.passes ? (unsigned *)c->status[(p + 1) % 2].ptr : nullptr;
-        a.ticket = &c->d_ctl->tickets[1 + p];
+        a.gpref = (const unsigned *)c->gpref.ptr;
+        a.intra = (const unsigned *)c->intra.ptr;
         a.ctl = c->d_ctl;
-        KernelScope ks(c, in == gg::IN_GEN ? K_PASS_GEN : K_PASS,
-                       in == gg::IN_GEN ? 16.0 * nobj + 8.0 * count : 16.0 * count);
-        GG_CUDA(gg::launch_pass(a, sc.rbits, in, out, ntiles, c->stream));
+        KernelScope ks(c, gen_up ? K_DOWN_GEN : K_DOWN, gen_up ? 16.0 * nobj + 8.0 * count : 16.0 * count);
+        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_up ? gg::IN_GEN : gg::IN_PAIR, ntiles, c->stream));
     }
     return GRID_OK;
 }
@@ -614,8 +623,8 @@ void grid_ctx_destroy(grid_ctx *c)
     {
         DeviceGuard g(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
-        Scratch *all[] = {&c->recs, &c->k2status, &c->tile_obj, &c->splits, &c->keys_sorted, &c->packed[0],
-                          &c->packed[1], &c->status[0], &c->status[1], &c->in_verts, &c->in_tris,
+        Scratch *all[] = {&c->recs, &c->k2status, &c->tile_obj, &c->splits, &c->keys_sorted, &c->keys[0],
+                          &c->vals[0], &c->intra, &c->gpref, &c->gstatus, &c->in_verts, &c->in_tris,
                           &c->out_cells, &c->out_refs};
         for (Scratch *s : all) release(c, *s);
         if (c->stream) cudaStreamSynchronize(c->stream);
