@@ -57,6 +57,7 @@ extern "C" {
 #define GRID_ECUDA (-6)      /* a CUDA runtime call failed */
 #define GRID_ENOSPC (-7)     /* caller's host buffer too small; info holds the sizes */
 #define GRID_ENOTREADY (-8)  /* serving: result not finished yet */
+#define GRID_ELIMIT (-9)     /* request larger than a fixed-size scratch buffer allows */
 
 #define GRID_RES_MAX 65535
 
@@ -195,6 +196,34 @@ int grid_sort_pairs(grid_ctx *ctx, const int32_t *C, const int32_t *O, int64_t c
  * cells (int32 [ncells + 1]), cells[c] = number of entries < c. */
 int grid_extract_ranges(grid_ctx *ctx, const int32_t *C_sorted, int64_t count, int64_t ncells,
                         int32_t *cells);
+
+/* ---- without allocation -------------------------------------------------- */
+
+/* The range extraction of grid_extract_ranges for callers that cannot
+ * allocate device memory when they call it: code running under another
+ * runtime's memory manager, loops where cudaMalloc / cudaFree would
+ * synchronise the device, paths that must not fail for lack of memory once
+ * initialised.  The paper has no counterpart; this is a deployment entry
+ * point.  It needs no context and allocates nothing: its scratch (a merge-path
+ * split table of 2^18 + 1 words, 1 MiB, and an error word) is a fixed-size
+ * device array of the library that every GPU which loads the library keeps
+ * until the process exits.
+ *
+ * C_sorted (int32 [count], cell ids sorted ascending, each < ncells) and
+ * cells (int32 [ncells + 1]) are device pointers on the calling thread's
+ * current device; the work runs on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream) and the call returns after it has finished.  The
+ * first call on a device looks up the scratch's device address; make that
+ * first call before any stream capture.  All calls share the one scratch
+ * array, which keeps the last call's contents: calls that overlap on the GPU
+ * (different streams or threads at the same time) race and must be
+ * serialised by the caller.
+ *
+ * Limit: count + ncells + 1 <= 2^18 * 2048 (about 5.4e8); larger requests
+ * return GRID_ELIMIT without touching the GPU.  GRID_EINVAL for bad
+ * arguments or a key >= ncells, GRID_ECUDA for a failed CUDA call. */
+int grid_extract_ranges_noalloc(const int32_t *C_sorted, int64_t count, int64_t ncells, int32_t *cells,
+                                void *stream);
 
 #ifdef __cplusplus
 }

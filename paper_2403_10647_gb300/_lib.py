@@ -17,6 +17,7 @@ GRID_ETIMEOUT = -5
 GRID_ECUDA = -6
 GRID_ENOSPC = -7
 GRID_ENOTREADY = -8
+GRID_ELIMIT = -9
 GRID_RES_MAX = 65535
 
 c_int32, c_int64, c_float, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
@@ -71,6 +72,7 @@ SIGNATURES = {
     "grid_emit_pairs": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, P(GridInfo), c_void_p, c_void_p]),
     "grid_sort_pairs": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p]),
     "grid_extract_ranges": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
+    "grid_extract_ranges_noalloc": (c_int32, [c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
 }
 
 _lib = None

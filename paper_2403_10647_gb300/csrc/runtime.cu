@@ -567,6 +567,7 @@ const char *grid_strerror(int code)
     case GRID_ECUDA: return "CUDA runtime error";
     case GRID_ENOSPC: return "host output buffer too small";
     case GRID_ENOTREADY: return "result not ready";
+    case GRID_ELIMIT: return "request exceeds the fixed scratch capacity of the allocation-free entry point";
     default: return "unknown error";
     }
 }
