@@ -33,7 +33,7 @@ WORKLOAD = "architectural_1e7"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--radix-bits", type=int, default=0)
@@ -62,7 +62,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -108,17 +108,27 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernels_digest() -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2403_10647_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel: str, nrefs: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
-    to this launch's pair count; None if no summary covers the current kernel."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summary profiles/dram_traffic.txt (lines: kernel, DRAM bytes per pair,
+    digest of the kernel source it was measured on), scaled to this launch's
+    pair count; None if no line covers the kernel as it is now."""
     try:
-        with open(path) as f:
-            t = json.load(f)
-        e = t[kernel]
-        return e["dram_bytes_per_pair"] * nrefs
-    except (OSError, KeyError, ValueError, TypeError):
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
+            lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    except OSError:
         return None
+    digest = kernels_digest()
+    for fields in lines:
+        if len(fields) >= 3 and fields[0] == kernel and fields[2] == digest:
+            return float(fields[1]) * nrefs
+    return None
 
 
 def make_scene():
