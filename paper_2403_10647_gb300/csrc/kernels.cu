@@ -620,31 +620,35 @@ __device__ __forceinline__ unsigned pad16(unsigned e) { return e + (e >> 4); }
 template <int T>
 __host__ __device__ constexpr int padded16() { return T + T / 16; }
 
-// The peer masks of the ranking step live inside the staging buffer, which
-// is idle while a tile is being ranked: items go through the ranking steps
-// in batches of 4, 2 or 1, the largest whose masks fit there (0: even one
-// batch does not fit, and four separate mask buffers follow the counts).
+// Peer masks of the ranking step: one word per (warp, digit) per item of a
+// batch.  When a batch of them fits in the staging buffer, which is idle
+// while a tile is being ranked, they live there and items go through the
+// ranking steps in batches of 4, 2 or 1 (the largest that fits); otherwise
+// they get shared memory of their own and items go one at a time.
+template <int BLOCK, int ITEMS, int RBITS>
+__host__ __device__ constexpr bool masks_alias()
+{
+    return (BLOCK / 32) * (1 << RBITS) * 4 <= padded16<BLOCK * ITEMS>() * 8;
+}
+
 template <int BLOCK, int ITEMS, int RBITS>
 __host__ __device__ constexpr int mask_batch()
 {
     return (4 * (BLOCK / 32) * (1 << RBITS) * 4 <= padded16<BLOCK * ITEMS>() * 8)   ? 4
            : (2 * (BLOCK / 32) * (1 << RBITS) * 4 <= padded16<BLOCK * ITEMS>() * 8) ? 2
-           : ((BLOCK / 32) * (1 << RBITS) * 4 <= padded16<BLOCK * ITEMS>() * 8)     ? 1
-                                                                                     : 0;
+                                                                                     : 1;
 }
 
-template <int BLOCK, int ITEMS, int RBITS>
-__host__ __device__ constexpr bool masks_in_stage()
-{
-    return mask_batch<BLOCK, ITEMS, RBITS>() > 0;
-}
-
+// Shared memory of one downsweep block: staging (64-bit elements; the object
+// marks and, when they fit, the peer masks alias it), input values, peer
+// masks when they do not fit, 16-bit warp digit counts, digit starts, global
+// bases.
 template <int BLOCK, int ITEMS, int RBITS>
 __host__ __device__ constexpr size_t down_smem_bytes()
 {
-    return sizeof(unsigned long long) * padded16<BLOCK * ITEMS>() +
-           sizeof(unsigned) * ((masks_in_stage<BLOCK, ITEMS, RBITS>() ? 1 : 5) * (BLOCK / 32) * (1 << RBITS) +
-                               2 * (1 << RBITS) + BLOCK / 32);
+    return sizeof(unsigned long long) * padded16<BLOCK * ITEMS>() + sizeof(unsigned) * BLOCK * ITEMS +
+           (masks_alias<BLOCK, ITEMS, RBITS>() ? 0 : sizeof(unsigned) * (BLOCK / 32) * (1 << RBITS)) +
+           sizeof(unsigned short) * (BLOCK / 32) * (1 << RBITS) + sizeof(unsigned) * (2 * (1 << RBITS) + BLOCK / 32);
 }
 
 __device__ __forceinline__ unsigned long long pack_kv(unsigned k, unsigned v)
@@ -652,84 +656,98 @@ __device__ __forceinline__ unsigned long long pack_kv(unsigned k, unsigned v)
     return ((unsigned long long)k << 32) | v;
 }
 
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <int BLOCK, int ITEMS, int RBITS, int IN>
-__global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownArgs a)
+__global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownArgs a, unsigned ntiles)
 {
     constexpr int W = BLOCK / 32;
     constexpr int T = BLOCK * ITEMS;
     constexpr int R = 1 << RBITS;
+    constexpr bool ALIAS = masks_alias<BLOCK, ITEMS, RBITS>();
+    constexpr int BATCH = ALIAS ? mask_batch<BLOCK, ITEMS, RBITS>() : 1;
+    static_assert(ITEMS % 2 == 0 && ITEMS % BATCH == 0 && T < 65536, "16-bit ranks and counts");
+    static_assert(!ALIAS || BATCH * W * R * 4 <= padded16<T>() * 8, "aliased peer masks fit in the staging buffer");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long *s_elem = reinterpret_cast<unsigned long long *>(smem_raw);   // [padded16 T]
-    unsigned *s_mark = reinterpret_cast<unsigned *>(smem_raw);   // object marks while generating (aliases s_elem)
-    constexpr bool ALIAS = masks_in_stage<BLOCK, ITEMS, RBITS>();
-    unsigned *s_whist = reinterpret_cast<unsigned *>(s_elem + padded16<T>());      // [W][R] warp digit counts
-    constexpr int BATCH = ALIAS ? mask_batch<BLOCK, ITEMS, RBITS>() : 4;
-    unsigned *s_wmask = ALIAS ? reinterpret_cast<unsigned *>(smem_raw) : s_whist + W * R;   // [BATCH][W][R] peer masks
-    unsigned *s_dstart = s_whist + (ALIAS ? 1 : 5) * W * R;   // [R]
+    unsigned long long *s_elem = reinterpret_cast<unsigned long long *>(smem_raw);   // [padded16 T] staging
+    unsigned *s_mark = reinterpret_cast<unsigned *>(smem_raw);       // object marks while generating
+    unsigned *s_vin = reinterpret_cast<unsigned *>(s_elem + padded16<T>());   // [T] values, element order
+    unsigned *s_wmask = ALIAS ? reinterpret_cast<unsigned *>(smem_raw) : s_vin + T;   // [BATCH][W][R] peer masks
+    unsigned short *s_wh = reinterpret_cast<unsigned short *>(s_vin + T + (ALIAS ? 0 : W * R));   // [W][R] warp counts
+    unsigned *s_wh32 = reinterpret_cast<unsigned *>(s_wh);                    // the same, as words
+    unsigned *s_dstart = reinterpret_cast<unsigned *>(s_wh + W * R);          // [R]
     unsigned *s_gbase = s_dstart + R;           // [R]
     unsigned *s_tmp = s_gbase + R;              // [W]
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const unsigned tile = blockIdx.x;
-    const unsigned group = tile / GROUP_TILES;
     const unsigned nd = 1u << a.bits;
-    for (int i = tid; i < W * R; i += BLOCK) s_whist[i] = 0u;
-    if (!ALIAS || IN != IN_GEN)   // generated tiles pass through the staging buffer first
-        for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
+    const unsigned sh = a.shift, mk = nd - 1u;
+    const unsigned ltmask = lanemask_lt();
+    const unsigned bit = 1u << lane;
+    const unsigned tile = blockIdx.x;
+    (void)ntiles;
+    const unsigned group = tile / GROUP_TILES;
+    const unsigned j0 = tile * (unsigned)T;
+    const unsigned cnt = min((unsigned)T, a.count - j0);
+    for (int i = tid; i < W * R / 2; i += BLOCK) s_wh32[i] = 0u;
     for (int d = tid; d < R; d += BLOCK)
         s_gbase[d] = d < (int)nd ? __ldg(a.dbase + d) + __ldg(a.gpref + (size_t)group * R + d) +
                                        __ldg(a.intra + (size_t)tile * R + d)
                                  : 0u;
-    const unsigned j0 = tile * (unsigned)T;
-    const unsigned cnt = min((unsigned)T, a.count - j0);
-    const unsigned sh = a.shift, mk = nd - 1u;
 
-    // element of item i for this lane (warp-striped): e = w * 32 * ITEMS + i * 32 + lane
-    unsigned keys[ITEMS], vals[ITEMS];
+    // keys of this lane's items in registers, values in shared memory;
+    // item i of this lane is element e = w * 32 * ITEMS + i * 32 + lane
+    unsigned keys[ITEMS];
     if (IN == IN_GEN) {
+        unsigned objs[ITEMS];
         __syncthreads();
         const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, tile, j0, cnt, s_mark, s_tmp);
-        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, vals);
+        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) s_elem[pad16(tid * ITEMS + i)] = pack_kv(keys[i], vals[i]);
+        for (int i = 0; i < ITEMS; ++i) s_elem[pad16(tid * ITEMS + i)] = pack_kv(keys[i], objs[i]);
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-            const unsigned long long v = s_elem[pad16(w * 32 * ITEMS + i * 32 + lane)];
+            const unsigned e = w * 32 * ITEMS + i * 32 + lane;
+            const unsigned long long v = s_elem[pad16(e)];
             keys[i] = (unsigned)(v >> 32);
-            vals[i] = (unsigned)v;
+            s_vin[e] = (unsigned)v;
         }
-        if (ALIAS) {
-            __syncthreads();   // the staging buffer is read out; the masks may take it
-            for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
-        }
+        __syncthreads();   // the staging buffer is read out; the masks take it
     } else {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const unsigned e = w * 32 * ITEMS + i * 32 + lane;
+            if (e < cnt) cp_async4(&s_vin[e], a.vals_in + j0 + e);
+        }
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const unsigned e = w * 32 * ITEMS + i * 32 + lane;
             keys[i] = e < cnt ? __ldcs(a.keys_in + j0 + e) : 0u;
         }
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-            vals[i] = e < cnt ? __ldcs(a.vals_in + j0 + e) : 0u;
-        }
     }
+    for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
     __syncthreads();
 
-    // warp-level multisplit, stable in element order (items in order, lanes in
-    // order): the lanes holding digit d find each other by OR-ing their lane
-    // bit into a shared mask word for d; the lowest of them reserves the
-    // group's slots in the warp's digit count with one shared atomic and the
-    // old count is broadcast.  BATCH items go through each step together so
-    // their shared-memory round trips overlap; the reservations are issued in
+    // warp-level multisplit, stable in element order (items in order,
+    // lanes in order): the lanes holding digit d find each other by
+    // OR-ing their lane bit into a shared mask word for d; the lowest of
+    // them reserves the group's slots in the warp's 16-bit digit count
+    // with one shared atomic, clears the mask word, and the old count is
+    // broadcast.  BATCH items go through each step together so their
+    // shared-memory round trips overlap; the reservations are issued in
     // item order, which keeps the ranks stable.
-    static_assert(ITEMS % 2 == 0 && ITEMS % BATCH == 0 && T <= 65536, "ranks are packed in 16-bit pairs");
     unsigned ranks[ITEMS / 2];   // 16-bit ranks, two per register
-    unsigned *wh = s_whist + w * R;
-    const unsigned ltmask = lanemask_lt();
-    const unsigned bit = 1u << lane;
 #pragma unroll
     for (int ib = 0; ib < ITEMS; ib += BATCH) {
         unsigned d[BATCH], peers[BATCH], old[BATCH];
@@ -749,7 +767,9 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
         for (int q = 0; q < BATCH; ++q) {
             old[q] = 0u;
             if (ok[q] && (peers[q] & ltmask) == 0u) {
-                old[q] = atomicAdd(&wh[d[q]], __popc(peers[q]));
+                const unsigned hs = (d[q] & 1u) * 16u;
+                old[q] = (atomicAdd(&s_wh32[(w * R + d[q]) >> 1], (unsigned)__popc(peers[q]) << hs) >> hs) &
+                         0xFFFFu;
                 s_wmask[(q * W + w) * R + d[q]] = 0u;
             }
         }
@@ -772,8 +792,8 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
         unsigned sum = 0;
 #pragma unroll
         for (int ww = 0; ww < W; ++ww) {
-            const unsigned c = s_whist[ww * R + d];
-            s_whist[ww * R + d] = sum;
+            const unsigned c = s_wh[ww * R + d];
+            s_wh[ww * R + d] = (unsigned short)sum;
             sum += c;
         }
         s_dstart[d] = sum;
@@ -800,9 +820,7 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
             ex += loc[k];
         }
     }
-    __syncthreads();
-    // each warp's slot base per digit: local digit start + earlier warps' share
-    for (int i = tid; i < W * R; i += BLOCK) s_whist[i] += s_dstart[i % R];
+    if (IN != IN_GEN) cp_async_wait_all();
     __syncthreads();
     // stage the tile in shared memory in locally sorted order
 #pragma unroll
@@ -811,7 +829,11 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
         if (e < cnt) {
             const unsigned d = (keys[i] >> sh) & mk;
             const unsigned rk = (ranks[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
-            s_elem[s_whist[w * R + d] + rk] = pack_kv(keys[i], vals[i]);
+            const unsigned pos = s_dstart[d] + s_wh[w * R + d] + rk;
+            if (pos < cnt)
+                s_elem[pos] = pack_kv(keys[i], s_vin[e]);
+            else
+                atomicOr(&a.ctl->err, ERR_RANGE);   // never with consistent counts
         }
     }
     __syncthreads();
@@ -968,18 +990,19 @@ static cudaError_t launch_up_t(const UpArgs &a, cudaStream_t s)
 }
 
 template <int RBITS, int IN>
-static cudaError_t launch_down_t(const DownArgs &a, unsigned ntiles, cudaStream_t s)
+static cudaError_t launch_down_t(const DownArgs &a, unsigned ntiles, int nsm, cudaStream_t s)
 {
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
     auto k = downsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, IN>;
     constexpr size_t smem = down_smem_bytes<PAIR_BLOCK, ITEMS, RBITS>();
     static bool configured = false;
+    (void)nsm;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k<<<ntiles, PAIR_BLOCK, smem, s>>>(a);
+    k<<<ntiles, PAIR_BLOCK, smem, s>>>(a, ntiles);
     return cudaGetLastError();
 }
 
@@ -1000,12 +1023,12 @@ cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s)
 #undef GG_UP
 }
 
-cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, cudaStream_t s)
+cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, int nsm, cudaStream_t s)
 {
     if (ntiles == 0) return cudaSuccess;
 #define GG_DOWN(RB)                                                        \
     case RB:                                                               \
-        return in == IN_GEN ? launch_down_t<RB, IN_GEN>(a, ntiles, s) : launch_down_t<RB, IN_PAIR>(a, ntiles, s);
+        return in == IN_GEN ? launch_down_t<RB, IN_GEN>(a, ntiles, nsm, s) : launch_down_t<RB, IN_PAIR>(a, ntiles, nsm, s);
     switch (rbits) {
         GG_DOWN(8)
         GG_DOWN(9)

@@ -14,10 +14,10 @@ namespace gg {
 #define GG_PAIR_BLOCK 256
 #endif
 #ifndef GG_PAIR_ITEMS
-#define GG_PAIR_ITEMS 16
+#define GG_PAIR_ITEMS 12
 #endif
 #ifndef GG_PASS_MIN_BLOCKS
-#define GG_PASS_MIN_BLOCKS 3
+#define GG_PASS_MIN_BLOCKS 4
 #endif
 #ifndef GG_GROUP_TILES
 #define GG_GROUP_TILES 16
@@ -113,7 +113,7 @@ cudaError_t launch_tile_search(const ObjRec *recs, long long n, unsigned tile, u
                                unsigned *tile_obj, cudaStream_t s);
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s);
 cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s);
-cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, cudaStream_t s);
+cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, int nsm, cudaStream_t s);
 unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells);
 cudaError_t launch_extract_split(const ExtractArgs &a, cudaStream_t s);
 cudaError_t launch_extract(const ExtractArgs &a, cudaStream_t s);

@@ -372,7 +372,7 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         a.intra = (const unsigned *)c->intra.ptr;
         a.ctl = c->d_ctl;
         KernelScope ks(c, gen_up ? K_DOWN_GEN : K_DOWN, gen_up ? 16.0 * nobj + 8.0 * count : 16.0 * count);
-        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_up ? gg::IN_GEN : gg::IN_PAIR, ntiles, c->stream));
+        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_up ? gg::IN_GEN : gg::IN_PAIR, ntiles, c->nsm, c->stream));
     }
     return GRID_OK;
 }

@@ -277,3 +277,37 @@ def test_full_size_configs(ctx, name):
     s = scenes.CONFIGS[name]()
     g, o = build_both(ctx, s, method="counting")
     assert_grid_equal(g, o, name)
+
+
+@pytest.mark.parametrize("radix_bits,key_bits", [(10, 20), (10, 30), (11, 11), (11, 22), (11, 31)])
+@pytest.mark.parametrize("count", [5_000, 4096 * 37 + 5, 1_500_001])
+def test_sort_wide_digits(radix_bits, key_bits, count):
+    """The 10- and 11-bit digit kernels (peer masks outside the staging
+    buffer when they do not fit) against a stable sort."""
+    import paper_2403_10647_gb300 as pg
+    g = np.random.Generator(np.random.Philox(radix_bits * 1000 + key_bits + count))
+    C = g.integers(0, 1 << key_bits, count).astype(np.int64).astype(np.int32)
+    O = np.arange(count, dtype=np.int32)
+    c = pg.Context(0, radix_bits=radix_bits)
+    try:
+        Cs, Os = c.sort_pairs(dev(C, torch.int32), dev(O, torch.int32), key_bits)
+    finally:
+        c.close()
+    perm = np.argsort(C, kind="stable")
+    assert np.array_equal(host(Cs), C[perm]) and np.array_equal(host(Os), O[perm])
+
+
+@pytest.mark.parametrize("radix_bits,lam", [(10, 6.0), (11, 24.0)])
+def test_wide_digits_full_build(radix_bits, lam):
+    """Whole builds whose keys split into two digits of exactly radix_bits
+    bits (20-bit keys at 10, 22-bit keys at 11)."""
+    import paper_2403_10647_gb300 as pg
+    s = scenes.nonhomogeneous_soup(100_000, seed=31, extent=46.0, lam=lam)
+    c = pg.Context(0, radix_bits=radix_bits)
+    try:
+        g = c.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+        assert g.info.key_bits == 2 * radix_bits
+        o = oracle.build_grid(s.verts, s.tris, s.lam, method="counting")
+        assert_grid_equal(g, o, f"radix {radix_bits}")
+    finally:
+        c.close()
