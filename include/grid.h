@@ -115,7 +115,8 @@ const char *grid_version(void);
  * records the kernel's algorithmic bytes (the bytes the step must move:
  * inputs read once, outputs written once).  Launches are counted always. */
 typedef struct {
-    char name[32];        /* kernel family: bounds, count_scan, tile_search, emit, hist, pass_gen, pass, extract */
+    char name[32];        /* kernel family: bounds, count_scan, tile_search, emit, upsweep_gen,
+                             downsweep_gen, upsweep, downsweep, extract_split, extract, localize */
     int64_t launches;
     double total_ms;      /* sum of event-timed durations (0 when profiling is off) */
     double bytes;         /* sum of algorithmic bytes */
@@ -154,6 +155,32 @@ int grid_build_host(grid_ctx *ctx, const float *h_verts, int64_t nverts, const i
                     int32_t *h_refs, int64_t refs_cap, grid_info *info);
 
 void grid_buf_free(grid_ctx *ctx, grid_buf *buf);
+
+/* ---- many meshes in one build ---------------------------------------------- */
+
+/* One mesh of a batch: device pointers as in grid_build, its own lambda. */
+typedef struct {
+    const float *verts;   /* [nverts][3] */
+    int64_t nverts;
+    const int32_t *tris;  /* [n][3] */
+    int64_t n;
+    float lambda;
+    int32_t reserved;
+} grid_mesh;
+
+/* BuildParallelGrid (Algorithm 1) of every mesh of a batch at once: the
+ * meshes' triangles and pairs form one flattened problem (one launch per step
+ * for the whole batch), keyed by (mesh, cell) so one stable sort orders every
+ * mesh's pairs.  The result per mesh is bit-identical to grid_build of that
+ * mesh alone.  out_cells holds every mesh's cells array back to back (mesh
+ * m's int32 [ncells_m + 1] at cells_offsets[m], values local to the mesh);
+ * out_refs every mesh's refs (int32 [nrefs_m] at refs_offsets[m], object ids
+ * local to the mesh).  infos[m] gets mesh m's metadata and sizes.  The sum of
+ * the meshes' cells and the sum of their pairs must each fit int32
+ * (GRID_EOVERFLOW); errors as grid_build.  Synchronises the stream twice
+ * (bounds, pair count) and at the end. */
+int grid_build_batched(grid_ctx *ctx, const grid_mesh *meshes, int32_t nmeshes, grid_buf *out_cells,
+                       grid_buf *out_refs, grid_info *infos, int64_t *cells_offsets, int64_t *refs_offsets);
 
 /* ---- the steps one by one (device pointers, caller-allocated outputs) ----- */
 

@@ -153,6 +153,35 @@ class Context:
                                    ctypes.byref(cb), ctypes.byref(rb), ctypes.byref(info)), "grid_build")
         return Grid(self._wrap(cb), self._wrap(rb), Info.from_c(info))
 
+    def build_batched(self, meshes) -> list:
+        """BuildParallelGrid of every (verts, tris, lam) in `meshes` at once.
+        Returns one Grid per mesh whose cells / refs are views into two
+        library buffers (bit-identical to building each mesh alone)."""
+        torch = self._torch
+        keep = []
+        arr = (_lib.GridMesh * len(meshes))()
+        for m, (verts, tris, lam) in enumerate(meshes):
+            v = self._dev(verts, torch.float32, 3)
+            t = self._dev(tris, torch.int32, 3)
+            keep += [v, t]
+            arr[m].verts, arr[m].nverts = v.data_ptr(), v.shape[0]
+            arr[m].tris, arr[m].n, arr[m].lam = t.data_ptr(), t.shape[0], float(lam)
+        nm = len(meshes)
+        infos = (GridInfo * nm)()
+        coff = (ctypes.c_int64 * nm)()
+        roff = (ctypes.c_int64 * nm)()
+        cb, rb = GridBuf(), GridBuf()
+        self._bind_stream()
+        check(self._lib.grid_build_batched(self._h, arr, nm, ctypes.byref(cb), ctypes.byref(rb), infos, coff, roff),
+              "grid_build_batched")
+        cells, refs = self._wrap(cb), self._wrap(rb)
+        out = []
+        for m in range(nm):
+            info = Info.from_c(infos[m])
+            c0, r0 = int(coff[m]), int(roff[m])
+            out.append(Grid(cells[c0:c0 + info.ncells + 1], refs[r0:r0 + info.nrefs], info))
+        return out
+
     def build_host(self, verts, tris, lam: float, cells_out=None, refs_out=None):
         """The same build from/to host memory (numpy arrays or CPU tensors,
         pinned for asynchronous copies).  Returns (cells, refs, info); the

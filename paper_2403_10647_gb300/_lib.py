@@ -41,6 +41,11 @@ class GridBuf(ctypes.Structure):
     _fields_ = [("ptr", c_void_p), ("count", c_int64), ("bytes", ctypes.c_size_t)]
 
 
+class GridMesh(ctypes.Structure):
+    _fields_ = [("verts", c_void_p), ("nverts", c_int64), ("tris", c_void_p), ("n", c_int64),
+                ("lam", c_float), ("reserved", c_int32)]
+
+
 class GridKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", c_int64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -64,6 +69,8 @@ SIGNATURES = {
                              P(GridInfo)]),
     "grid_build_host": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_float, c_void_p, c_int64,
                                   c_void_p, c_int64, P(GridInfo)]),
+    "grid_build_batched": (c_int32, [c_void_p, P(GridMesh), c_int32, P(GridBuf), P(GridBuf), P(GridInfo),
+                                     P(c_int64), P(c_int64)]),
     "grid_buf_free": (None, [c_void_p, P(GridBuf)]),
     "grid_bounds": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, P(c_float), P(c_float)]),
     "grid_plan": (c_int32, [P(c_float), P(c_float), c_int64, c_float, P(GridInfo)]),

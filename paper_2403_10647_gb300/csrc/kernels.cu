@@ -133,6 +133,21 @@ __device__ __forceinline__ unsigned tile_objects(const ObjRec *__restrict__ recs
     return of;
 }
 
+// Batched builds: the mesh owning object o (largest m with obj_base[m] <= o;
+// empty meshes own no object).
+__device__ __forceinline__ int mesh_of(const MeshTab &mt, long long o)
+{
+    int lo = 0, hi = mt.nm - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(mt.obj_base + mid) <= o)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // SegmentedExclusiveSum + MakeCellIds (GlobalCoords, Sec. 3) for the ITEMS
 // consecutive pairs e = tid * ITEMS + i of a tile (blocked arrangement).  The
 // relative offset rid = j - start is decomposed with divisions only for the
@@ -140,13 +155,16 @@ __device__ __forceinline__ unsigned tile_objects(const ObjRec *__restrict__ recs
 // consecutive, and a pair whose object differs from its predecessor's is that
 // object's first pair (rid = 0), so every other pair advances (x, y, z) by one
 // step, x fastest.
+// In a batched build (mt.md set) each object's mesh supplies the grid
+// strides, the key offset cell_base and the object-id offset.
 template <int ITEMS>
 __device__ __forceinline__ void gen_blocked(const ObjRec *__restrict__ recs, unsigned of, const unsigned *mark,
                                             unsigned j0, unsigned cnt, unsigned res_x, unsigned res_y,
-                                            unsigned (&keys)[ITEMS], unsigned (&objs)[ITEMS])
+                                            const MeshTab &mt, unsigned (&keys)[ITEMS], unsigned (&objs)[ITEMS])
 {
     const unsigned e0 = threadIdx.x * ITEMS;
     unsigned o = 0u, x = 0u, y = 0u, z = 0u, mx = 1u, my = 1u, lox = 0u, loy = 0u, loz = 0u;
+    unsigned rx = res_x, ry = res_y, kbase = 0u, obase = 0u;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const unsigned e = e0 + i;
@@ -162,6 +180,13 @@ __device__ __forceinline__ void gen_blocked(const ObjRec *__restrict__ recs, uns
                 loz = r.y & 0xFFFFu;
                 mx = (r.y >> 16) - lox + 1u;
                 my = (r.z & 0xFFFFu) - loy + 1u;
+                if (mt.md) {
+                    const int m = mesh_of(mt, o);
+                    rx = (unsigned)__ldg(&mt.md[m].res[0]);
+                    ry = (unsigned)__ldg(&mt.md[m].res[1]);
+                    kbase = __ldg(&mt.md[m].cell_base);
+                    obase = (unsigned)__ldg(mt.obj_base + m);
+                }
                 if (i == 0) {
                     const unsigned rid = j0 + e - r.w;
                     const unsigned mxy = mx * my;
@@ -179,8 +204,8 @@ __device__ __forceinline__ void gen_blocked(const ObjRec *__restrict__ recs, uns
                     ++z;
                 }
             }
-            keys[i] = (lox + x) + res_x * ((loy + y) + res_y * (loz + z));
-            objs[i] = o;
+            keys[i] = kbase + (lox + x) + rx * ((loy + y) + ry * (loz + z));
+            objs[i] = o - obase;
         }
     }
 }
@@ -281,12 +306,33 @@ __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
         unsigned V = 0u;
         rec[i] = make_uint4(0u, 0u, 0u, 0u);
         if (o < a.n) {
+            // the triangle and the grid it maps into: the single mesh's, or
+            // in a batched build the owning mesh's
+            const int *tris = a.tris;
+            const float *verts = a.verts;
+            long long nverts = a.nverts, lo_obj = o;
+            float glo[3] = {a.lo[0], a.lo[1], a.lo[2]}, gsc[3] = {a.scale[0], a.scale[1], a.scale[2]};
+            int gres[3] = {a.res[0], a.res[1], a.res[2]};
+            if (a.mt.md) {
+                const int m = mesh_of(a.mt, o);
+                const MeshDesc &md = a.mt.md[m];
+                tris = md.tris;
+                verts = md.verts;
+                nverts = md.nverts;
+                lo_obj = o - __ldg(a.mt.obj_base + m);
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    glo[ax] = md.lo[ax];
+                    gsc[ax] = md.scale[ax];
+                    gres[ax] = md.res[ax];
+                }
+            }
             int vi[3];
             bool ok = true;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                vi[k] = __ldg(a.tris + 3 * o + k);
-                ok = ok && vi[k] >= 0 && (long long)vi[k] < a.nverts;
+                vi[k] = __ldg(tris + 3 * lo_obj + k);
+                ok = ok && vi[k] >= 0 && (long long)vi[k] < nverts;
             }
             if (!ok) {  // never read outside verts: flag and use vertex 0
                 atomicOr(&a.ctl->err, ERR_BADINDEX);
@@ -295,13 +341,13 @@ __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
             unsigned clo[3], chi[3];
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
-                const float p0 = __ldg(a.verts + 3ll * vi[0] + ax);
-                const float p1 = __ldg(a.verts + 3ll * vi[1] + ax);
-                const float p2 = __ldg(a.verts + 3ll * vi[2] + ax);
+                const float p0 = __ldg(verts + 3ll * vi[0] + ax);
+                const float p1 = __ldg(verts + 3ll * vi[1] + ax);
+                const float p2 = __ldg(verts + 3ll * vi[2] + ax);
                 const float bl = fminf(fminf(p0, p1), p2);
                 const float bh = fmaxf(fmaxf(p0, p1), p2);
-                clo[ax] = (unsigned)cell_coord(bl, a.lo[ax], a.scale[ax], a.res[ax]);
-                chi[ax] = (unsigned)cell_coord(bh, a.lo[ax], a.scale[ax], a.res[ax]);
+                clo[ax] = (unsigned)cell_coord(bl, glo[ax], gsc[ax], gres[ax]);
+                chi[ax] = (unsigned)cell_coord(bh, glo[ax], gsc[ax], gres[ax]);
             }
             unsigned long long cnt = (unsigned long long)(chi[0] - clo[0] + 1u) *
                                      (unsigned long long)(chi[1] - clo[1] + 1u) *
@@ -364,6 +410,10 @@ __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
             uint4 r = rec[i];
             r.w = (unsigned)(excl + s_pref[i * BLOCK + tid]);
             reinterpret_cast<uint4 *>(a.recs)[o] = r;
+            if (a.mt.md) {
+                const int m = mesh_of(a.mt, o);
+                if (__ldg(a.mt.obj_base + m) == o) a.pair_base[m] = r.w;
+            }
         }
     }
 }
@@ -411,7 +461,7 @@ __global__ void __launch_bounds__(BLOCK) emit_kernel(EmitArgs a)
     const unsigned cnt = min((unsigned)T, a.count - j0);
     const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
     unsigned keys[ITEMS], objs[ITEMS];
-    gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
+    gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -515,7 +565,7 @@ __global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
         if (SRC == SRC_GEN) {
             unsigned objs[ITEMS];
             const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
-            gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
+            gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
         } else {
 #pragma unroll
             for (int i = 0; i < ITEMS; i += 4) {
@@ -711,7 +761,7 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
         unsigned objs[ITEMS];
         __syncthreads();
         const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, tile, j0, cnt, s_mark, s_tmp);
-        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, keys, objs);
+        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) s_elem[pad16(tid * ITEMS + i)] = pack_kv(keys[i], objs[i]);
@@ -926,6 +976,101 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// batched builds: per-mesh bounds, per-mesh cell arrays
+// ---------------------------------------------------------------------------
+
+// Each thread takes BOUNDS_ITEMS consecutive triangles of the flattened batch;
+// a warp whose triangles all belong to one mesh reduces in registers, other
+// warps update per lane.  bstate[m * 6 + a] holds ~ordered(min) for a < 3 and
+// ordered(max) for a >= 3 (both atomicMax).
+constexpr int BOUNDS_ITEMS = 8;
+
+__global__ void __launch_bounds__(256) bounds_batched_kernel(MeshTab mt, long long ntot, unsigned *bstate, Ctl *ctl)
+{
+    const long long t0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * BOUNDS_ITEMS;
+    const float inf = __int_as_float(0x7f800000);
+    float lo[3] = {inf, inf, inf}, hi[3] = {-inf, -inf, -inf};
+    unsigned err = 0;
+    int m0 = -1;
+    auto flush = [&](int m) {
+        if (m < 0) return;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (lo[a] <= hi[a]) {
+                atomicMax(&bstate[m * 6 + a], ~float_to_ordered(lo[a]));
+                atomicMax(&bstate[m * 6 + 3 + a], float_to_ordered(hi[a]));
+            }
+            lo[a] = inf;
+            hi[a] = -inf;
+        }
+    };
+    for (int k = 0; k < BOUNDS_ITEMS; ++k) {
+        const long long o = t0 + k;
+        if (o >= ntot) break;
+        const int m = mesh_of(mt, o);
+        if (m != m0) {
+            flush(m0);
+            m0 = m;
+        }
+        const MeshDesc &md = mt.md[m];
+        const long long li = o - __ldg(mt.obj_base + m);
+        for (int v = 0; v < 3; ++v) {
+            const int vi = __ldg(md.tris + 3 * li + v);
+            if (vi < 0 || (long long)vi >= md.nverts) {
+                err |= ERR_BADINDEX;
+                continue;
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float x = __ldg(md.verts + 3ll * vi + a);
+                if (!isfinite(x)) {
+                    err |= ERR_NONFINITE;
+                } else {
+                    lo[a] = fminf(lo[a], x);
+                    hi[a] = fmaxf(hi[a], x);
+                }
+            }
+        }
+    }
+    // one mesh for the whole warp: reduce in registers, one lane updates
+    const bool same = __all_sync(0xffffffffu, m0 == __shfl_sync(0xffffffffu, m0, 0));
+    if (same) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+                hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+            }
+        }
+        if ((threadIdx.x & 31) == 0) flush(m0);
+    } else {
+        flush(m0);
+    }
+    err = __reduce_or_sync(0xffffffffu, err);
+    if ((threadIdx.x & 31) == 0 && err) atomicOr(&ctl->err, err);
+}
+
+__global__ void __launch_bounds__(256) localize_kernel(const unsigned *__restrict__ G,
+                                                       const long long *__restrict__ cells_off,
+                                                       const unsigned *__restrict__ pair_base, int nm,
+                                                       long long total, unsigned *__restrict__ out)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= total) return;
+    int lo = 0, hi = nm - 1;   // mesh m: largest with cells_off[m] <= q (every slice is non-empty)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(cells_off + mid) <= q)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    // mesh m's cell k is global cell cell_base[m] + k = q - m (each earlier mesh has one extra entry)
+    out[q] = __ldg(G + (q - lo)) - __ldg(pair_base + lo);
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 
@@ -937,6 +1082,22 @@ cudaError_t launch_bounds(const float *verts, long long nverts, const int *tris,
     const long long cap = (long long)nsm * 8;
     if (blocks > cap) blocks = cap;
     bounds_kernel<<<(unsigned)blocks, 256, 0, s>>>(verts, nverts, tris, n, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds_batched(const MeshTab &mt, long long ntot, unsigned *bstate, Ctl *ctl, cudaStream_t s)
+{
+    if (ntot <= 0) return cudaSuccess;
+    const long long per_block = 256ll * BOUNDS_ITEMS;
+    bounds_batched_kernel<<<(unsigned)((ntot + per_block - 1) / per_block), 256, 0, s>>>(mt, ntot, bstate, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_localize(const unsigned *G, const long long *cells_off, const unsigned *pair_base, int nm,
+                            long long total, unsigned *out, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    localize_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(G, cells_off, pair_base, nm, total, out);
     return cudaGetLastError();
 }
 

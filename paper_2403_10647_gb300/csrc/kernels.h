@@ -33,6 +33,27 @@ constexpr int EXTRACT_TILE = 2048;
 
 enum { SRC_MEM = 0, SRC_GEN = 1 };
 
+// A batch of meshes built as one flattened problem: mesh m owns objects
+// [obj_base[m], obj_base[m + 1]) and global cell ids [cell_base,
+// cell_base + ncells); a pair's key is cell_base + its local cell id and its
+// value the object's index inside its mesh.
+struct MeshDesc {
+    const float *verts;
+    const int *tris;
+    long long nverts;
+    long long n;
+    float lo[3];
+    float scale[3];
+    int res[3];
+    unsigned cell_base;
+};
+
+struct MeshTab {
+    const MeshDesc *md;             // [nm] device; nullptr for a single mesh
+    const long long *obj_base;      // [nm + 1] device
+    int nm;
+};
+
 struct CountArgs {
     const float *verts;
     long long nverts;
@@ -44,11 +65,14 @@ struct CountArgs {
     ObjRec *recs;                   // [n] out
     unsigned long long *status;     // [ceil(n / COUNT_TILE)] look-back words, zeroed
     Ctl *ctl;
+    MeshTab mt;                     // batched: per-object mesh (verts, tris, plan)
+    unsigned *pair_base;            // batched: [nm] out, pair offset of each mesh's first object
 };
 
 struct EmitArgs {
     const ObjRec *recs;
     const unsigned *tile_obj;       // [ntiles + 1]
+    MeshTab mt;
     unsigned res_x, res_y;
     unsigned count;                 // NO
     unsigned *C;
@@ -63,6 +87,7 @@ struct UpArgs {
     const unsigned *keys_in;        // SRC_MEM
     const ObjRec *recs;             // SRC_GEN
     const unsigned *tile_obj;       // SRC_GEN
+    MeshTab mt;                     // SRC_GEN, batched
     unsigned res_x, res_y;          // SRC_GEN
     unsigned count;
     unsigned ntiles;
@@ -86,6 +111,7 @@ struct DownArgs {
     const unsigned *vals_in;        // IN_PAIR
     const ObjRec *recs;             // IN_GEN
     const unsigned *tile_obj;       // IN_GEN
+    MeshTab mt;                     // IN_GEN, batched
     unsigned res_x, res_y;          // IN_GEN
     unsigned *keys_out;
     unsigned *vals_out;
@@ -108,6 +134,12 @@ struct ExtractArgs {
 
 cudaError_t launch_bounds(const float *verts, long long nverts, const int *tris, long long n, Ctl *ctl,
                           int nsm, cudaStream_t s);
+// Batched: per-mesh bounds into bstate[m * 6 + (lo_inv x, y, z, hi x, y, z)].
+cudaError_t launch_bounds_batched(const MeshTab &mt, long long ntot, unsigned *bstate, Ctl *ctl, cudaStream_t s);
+// Batched: out[q] = G[q - m] - pair_base[m] for q in mesh m's slice
+// [cells_off[m], cells_off[m + 1]) of the per-mesh cell arrays.
+cudaError_t launch_localize(const unsigned *G, const long long *cells_off, const unsigned *pair_base, int nm,
+                            long long total, unsigned *out, cudaStream_t s);
 cudaError_t launch_count_scan(const CountArgs &a, cudaStream_t s);
 cudaError_t launch_tile_search(const ObjRec *recs, long long n, unsigned tile, unsigned ntiles,
                                unsigned *tile_obj, cudaStream_t s);

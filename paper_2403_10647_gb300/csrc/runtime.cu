@@ -44,10 +44,11 @@ struct Scratch {
 };
 
 enum KernelId {
-    K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_NUM
+    K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_LOCALIZE, K_NUM
 };
-const char *const kKernelNames[K_NUM] = {"bounds", "count_scan", "tile_search", "emit", "upsweep_gen",
-                                         "downsweep_gen", "upsweep", "downsweep", "extract_split", "extract"};
+const char *const kKernelNames[K_NUM] = {"bounds",  "count_scan",    "tile_search",   "emit",
+                                         "upsweep_gen", "downsweep_gen", "upsweep", "downsweep",
+                                         "extract_split", "extract",   "localize"};
 
 struct PendingTiming {
     int kid;
@@ -72,6 +73,7 @@ struct grid_ctx {
 
     Scratch recs, k2status, tile_obj, keys_sorted, keys[1], vals[1], intra, gpref, gstatus, splits;
     Scratch in_verts, in_tris, out_cells, out_refs;  // host-buffer builds
+    Scratch b_desc, b_base, b_state, b_pairbase, b_cellsoff, b_G;   // batched builds
     std::atomic<int64_t> in_use{0};
 
     // per-kernel accounting
@@ -304,8 +306,8 @@ unsigned pair_tiles(int64_t count) { return (unsigned)((count + gg::PAIR_TILE - 
 // pass outputs alternate between those and one scratch pair of arrays so
 // the last lands there.
 int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const ObjRec *recs, int64_t nobj,
-               const unsigned *tile_obj, unsigned res_x, unsigned res_y, const unsigned *keys_in,
-               const unsigned *vals_in, unsigned *keys_last, unsigned *vals_last)
+               const unsigned *tile_obj, unsigned res_x, unsigned res_y, const gg::MeshTab &mt,
+               const unsigned *keys_in, const unsigned *vals_in, unsigned *keys_last, unsigned *vals_last)
 {
     const unsigned ntiles = pair_tiles(count);
     const unsigned ngroups = (ntiles + gg::GROUP_TILES - 1) / gg::GROUP_TILES;
@@ -333,6 +335,7 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         u.keys_in = kin;
         u.recs = recs;
         u.tile_obj = tile_obj;
+        u.mt = mt;
         u.res_x = res_x;
         u.res_y = res_y;
         u.count = count;
@@ -360,6 +363,7 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         a.vals_in = vin;
         a.recs = recs;
         a.tile_obj = tile_obj;
+        a.mt = mt;
         a.res_x = res_x;
         a.res_y = res_y;
         a.keys_out = ko[p];
@@ -495,7 +499,7 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
             GG_CUDA(gg::launch_emit(ea, c->stream));
         } else {
             GG_TRY(sort_pairs(c, sc, count, true, recs, n, tile_obj, (unsigned)I.res[0], (unsigned)I.res[1],
-                              nullptr, nullptr, keys_sorted, refs));
+                              gg::MeshTab{}, nullptr, nullptr, keys_sorted, refs));
         }
         GG_TRY(extract_ranges(c, keys_sorted, count, I.ncells, cells));
     } else {
@@ -626,7 +630,8 @@ void grid_ctx_destroy(grid_ctx *c)
         if (c->stream) cudaStreamSynchronize(c->stream);
         Scratch *all[] = {&c->recs, &c->k2status, &c->tile_obj, &c->splits, &c->keys_sorted, &c->keys[0],
                           &c->vals[0], &c->intra, &c->gpref, &c->gstatus, &c->in_verts, &c->in_tris,
-                          &c->out_cells, &c->out_refs};
+                          &c->out_cells, &c->out_refs, &c->b_desc, &c->b_base, &c->b_state, &c->b_pairbase,
+                          &c->b_cellsoff, &c->b_G};
         for (Scratch *s : all) release(c, *s);
         if (c->stream) cudaStreamSynchronize(c->stream);
         resolve_timings(c);
@@ -730,6 +735,183 @@ int grid_build_host(grid_ctx *c, const float *h_verts, int64_t nverts, const int
                                 c->stream));
     GG_CUDA(cudaStreamSynchronize(c->stream));
     return GRID_OK;
+}
+
+int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, grid_buf *out_cells,
+                       grid_buf *out_refs, grid_info *infos, int64_t *cells_offsets, int64_t *refs_offsets)
+{
+    if (!c || !meshes || nmeshes < 1 || nmeshes > (1 << 20) || !out_cells || !out_refs || !infos ||
+        !cells_offsets || !refs_offsets)
+        return GRID_EINVAL;
+    *out_cells = grid_buf{nullptr, 0, 0};
+    *out_refs = grid_buf{nullptr, 0, 0};
+    DeviceGuard g(c->device);
+    const int nm = nmeshes;
+    std::vector<long long> obj_base(nm + 1, 0);
+    for (int m = 0; m < nm; ++m) {
+        const grid_mesh &mesh = meshes[m];
+        if (mesh.n < 0 || mesh.nverts < 0 || !valid_lambda(mesh.lambda)) return GRID_EINVAL;
+        if (mesh.n > 0 && (!mesh.verts || !mesh.tris)) return GRID_EINVAL;
+        obj_base[m + 1] = obj_base[m] + mesh.n;
+        if (obj_base[m + 1] > kInt32Max - 1) return GRID_EOVERFLOW;
+    }
+    const long long ntot = obj_base[nm];
+    std::vector<gg::MeshDesc> desc(nm);
+    for (int m = 0; m < nm; ++m) {
+        desc[m] = gg::MeshDesc{};
+        desc[m].verts = meshes[m].verts;
+        desc[m].tris = meshes[m].tris;
+        desc[m].nverts = meshes[m].nverts;
+        desc[m].n = meshes[m].n;
+    }
+    GG_TRY(ensure(c, c->b_desc, sizeof(gg::MeshDesc) * nm));
+    GG_TRY(ensure(c, c->b_base, sizeof(long long) * (nm + 1)));
+    GG_TRY(ensure(c, c->b_state, sizeof(unsigned) * 6 * nm));
+    GG_TRY(ensure(c, c->b_pairbase, sizeof(unsigned) * nm));
+    GG_TRY(ensure(c, c->b_cellsoff, sizeof(long long) * (nm + 1)));
+    gg::MeshTab mt{(const gg::MeshDesc *)c->b_desc.ptr, (const long long *)c->b_base.ptr, nm};
+    GG_TRY(reset_ctl(c));
+    GG_CUDA(cudaMemsetAsync(c->b_state.ptr, 0, sizeof(unsigned) * 6 * nm, c->stream));
+    GG_CUDA(cudaMemcpyAsync(c->b_desc.ptr, desc.data(), sizeof(gg::MeshDesc) * nm, cudaMemcpyHostToDevice,
+                            c->stream));
+    GG_CUDA(cudaMemcpyAsync(c->b_base.ptr, obj_base.data(), sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice,
+                            c->stream));
+
+    // a0: every mesh's scene bounds in one pass over the flattened triangles
+    {
+        KernelScope ks(c, K_BOUNDS, 48.0 * ntot);
+        GG_CUDA(gg::launch_bounds_batched(mt, ntot, (unsigned *)c->b_state.ptr, c->d_ctl, c->stream));
+    }
+    std::vector<unsigned> bstate(6 * (size_t)nm);
+    GG_CUDA(cudaMemcpyAsync(bstate.data(), c->b_state.ptr, sizeof(unsigned) * 6 * nm, cudaMemcpyDeviceToHost,
+                            c->stream));
+    GG_TRY(read_ctl(c));
+    GG_TRY(ctl_error(c->h_ctl->err));
+
+    // a1: each mesh's metadata; cell ids of mesh m start at cell_base[m]
+    std::vector<long long> cells_off(nm + 1, 0);
+    long long cell_base = 0;
+    for (int m = 0; m < nm; ++m) {
+        float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
+        if (meshes[m].n > 0) {
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = gg::ordered_to_float(~bstate[6 * m + a]);
+                hi[a] = gg::ordered_to_float(bstate[6 * m + 3 + a]);
+            }
+        }
+        GG_TRY(plan(lo, hi, meshes[m].n, meshes[m].lambda, &infos[m]));
+        for (int a = 0; a < 3; ++a) {
+            desc[m].lo[a] = infos[m].lo[a];
+            desc[m].scale[a] = infos[m].scale[a];
+            desc[m].res[a] = infos[m].res[a];
+        }
+        desc[m].cell_base = (unsigned)cell_base;
+        cell_base += infos[m].ncells;
+        if (cell_base > kInt32Max) return GRID_EOVERFLOW;
+        cells_off[m + 1] = cells_off[m] + infos[m].ncells + 1;
+    }
+    const long long ncells_all = cell_base;
+    GG_CUDA(cudaMemcpyAsync(c->b_desc.ptr, desc.data(), sizeof(gg::MeshDesc) * nm, cudaMemcpyHostToDevice,
+                            c->stream));
+
+    // a2 + a3 over all objects: one scan, so each mesh's pairs follow the last
+    const int64_t ctiles = (ntot + gg::COUNT_TILE - 1) / gg::COUNT_TILE;
+    unsigned *pair_base_d = (unsigned *)c->b_pairbase.ptr;
+    GG_CUDA(cudaMemsetAsync(pair_base_d, 0, sizeof(unsigned) * nm, c->stream));
+    if (ntot > 0) {
+        GG_TRY(ensure(c, c->recs, (size_t)ntot * sizeof(ObjRec)));
+        GG_TRY(ensure(c, c->k2status, (size_t)ctiles * 8));
+        GG_CUDA(cudaMemsetAsync(c->k2status.ptr, 0, (size_t)ctiles * 8, c->stream));
+        gg::CountArgs ca{};
+        ca.n = ntot;
+        ca.recs = (ObjRec *)c->recs.ptr;
+        ca.status = (unsigned long long *)c->k2status.ptr;
+        ca.ctl = c->d_ctl;
+        ca.mt = mt;
+        ca.pair_base = pair_base_d;
+        KernelScope ks(c, K_COUNT, 64.0 * ntot);
+        GG_CUDA(gg::launch_count_scan(ca, c->stream));
+    }
+    std::vector<unsigned> pair_base(nm + 1, 0);
+    GG_CUDA(cudaMemcpyAsync(pair_base.data(), pair_base_d, sizeof(unsigned) * nm, cudaMemcpyDeviceToHost,
+                            c->stream));
+    GG_TRY(read_ctl(c));
+    GG_TRY(ctl_error(c->h_ctl->err));
+    const int64_t NO = ntot > 0 ? (int64_t)c->h_ctl->nrefs : 0;
+    if (NO > kInt32Max) return GRID_EOVERFLOW;
+    pair_base[nm] = (unsigned)NO;
+    for (int m = nm - 1; m >= 0; --m)   // an empty mesh starts where the next one does
+        if (meshes[m].n == 0) pair_base[m] = pair_base[m + 1];
+    for (int m = 0; m < nm; ++m) {
+        infos[m].nrefs = (int64_t)pair_base[m + 1] - pair_base[m];
+        cells_offsets[m] = cells_off[m];
+        refs_offsets[m] = pair_base[m];
+    }
+
+    // outputs: every mesh's cells array back to back, refs back to back
+    const long long ncells_out = cells_off[nm];
+    void *pc = nullptr, *pr = nullptr;
+    GG_TRY(pool_alloc(c, (size_t)ncells_out * 4, &pc));
+    int rc = pool_alloc(c, (size_t)NO * 4, &pr);
+    if (rc != GRID_OK) {
+        pool_free(c, pc, (size_t)ncells_out * 4);
+        return rc;
+    }
+    *out_cells = grid_buf{pc, ncells_out, (size_t)ncells_out * 4};
+    *out_refs = grid_buf{pr, NO, (size_t)NO * 4};
+    rc = [&]() -> int {
+        GG_TRY(ensure(c, c->b_G, (size_t)(ncells_all + 1) * sizeof(unsigned)));
+        unsigned *G = (unsigned *)c->b_G.ptr;
+        if (NO > 0) {
+            const unsigned count = (unsigned)NO;
+            const unsigned ntiles = pair_tiles(count);
+            GG_TRY(ensure(c, c->tile_obj, (size_t)(ntiles + 1) * sizeof(unsigned)));
+            const ObjRec *recs = (const ObjRec *)c->recs.ptr;
+            unsigned *tile_obj = (unsigned *)c->tile_obj.ptr;
+            {
+                KernelScope ks(c, K_TILES, 4.0 * (ntiles + 1));
+                GG_CUDA(gg::launch_tile_search(recs, ntot, gg::PAIR_TILE, ntiles, tile_obj, c->stream));
+            }
+            GG_TRY(ensure(c, c->keys_sorted, (size_t)count * sizeof(unsigned)));
+            unsigned *keys_sorted = (unsigned *)c->keys_sorted.ptr;
+            int key_bits = 0;
+            for (unsigned long long v = (unsigned long long)(ncells_all - 1); v; v >>= 1) ++key_bits;
+            const SortCfg sc = sort_cfg(key_bits, c->rbits_max);
+            if (sc.passes == 0) {
+                gg::EmitArgs ea{};
+                ea.recs = recs;
+                ea.tile_obj = tile_obj;
+                ea.mt = mt;
+                ea.count = count;
+                ea.C = keys_sorted;
+                ea.O = (unsigned *)pr;
+                KernelScope ks(c, K_EMIT, 16.0 * ntot + 8.0 * count);
+                GG_CUDA(gg::launch_emit(ea, c->stream));
+            } else {
+                GG_TRY(sort_pairs(c, sc, count, true, recs, ntot, tile_obj, 0, 0, mt, nullptr, nullptr, keys_sorted,
+                                  (unsigned *)pr));
+            }
+            GG_TRY(extract_ranges(c, keys_sorted, count, ncells_all, G));
+        } else {
+            GG_CUDA(cudaMemsetAsync(G, 0, (size_t)(ncells_all + 1) * sizeof(unsigned), c->stream));
+        }
+        GG_CUDA(cudaMemcpyAsync(c->b_cellsoff.ptr, cells_off.data(), sizeof(long long) * (nm + 1),
+                                cudaMemcpyHostToDevice, c->stream));
+        GG_CUDA(cudaMemcpyAsync(pair_base_d, pair_base.data(), sizeof(unsigned) * nm, cudaMemcpyHostToDevice,
+                                c->stream));
+        {
+            KernelScope ks(c, K_LOCALIZE, 8.0 * ncells_out);
+            GG_CUDA(gg::launch_localize(G, (const long long *)c->b_cellsoff.ptr, pair_base_d, nm, ncells_out,
+                                        (unsigned *)pc, c->stream));
+        }
+        GG_TRY(read_ctl(c));
+        return ctl_error(c->h_ctl->err);
+    }();
+    if (rc != GRID_OK) {
+        grid_buf_free(c, out_cells);
+        grid_buf_free(c, out_refs);
+    }
+    return rc;
 }
 
 void grid_buf_free(grid_ctx *c, grid_buf *b)
@@ -850,7 +1032,7 @@ int grid_sort_pairs(grid_ctx *c, const int32_t *C, const int32_t *O, int64_t cou
         GG_CUDA(cudaMemcpyAsync(C_out, C, (size_t)count * 4, cudaMemcpyDeviceToDevice, c->stream));
         GG_CUDA(cudaMemcpyAsync(O_out, O, (size_t)count * 4, cudaMemcpyDeviceToDevice, c->stream));
     } else {
-        GG_TRY(sort_pairs(c, sc, (unsigned)count, false, nullptr, 0, nullptr, 0, 0, (const unsigned *)C,
+        GG_TRY(sort_pairs(c, sc, (unsigned)count, false, nullptr, 0, nullptr, 0, 0, gg::MeshTab{}, (const unsigned *)C,
                           (const unsigned *)O, (unsigned *)C_out, (unsigned *)O_out));
     }
     GG_TRY(read_ctl(c));

@@ -311,3 +311,67 @@ def test_wide_digits_full_build(radix_bits, lam):
         assert_grid_equal(g, o, f"radix {radix_bits}")
     finally:
         c.close()
+
+
+# ---- batched builds ---------------------------------------------------------------------
+
+def _mixed_batch():
+    g = np.random.Generator(np.random.Philox(4242))
+    return [
+        scenes.uniform_soup(5_000, seed=201),
+        scenes.Scene("empty", np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), 4.0),
+        _scene([[0, 0, 0], [1, 0.5, 0.2], [0.3, 1, 0.9]], [[0, 1, 2]], 64.0),
+        scenes.tiny_scene(g, 37),
+        scenes.nonhomogeneous_soup(20_000, seed=202, extent=25.0),
+        scenes.architectural(30_000, seed=203, size=(30.0, 8.0, 30.0), nblobs=20),
+        scenes.Scene("empty2", np.zeros((5, 3), np.float32), np.zeros((0, 3), np.int32), 2.0),
+    ]
+
+
+def test_batched_matches_oracle_and_plain(ctx):
+    batch = _mixed_batch()
+    grids = ctx.build_batched([(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam) for s in batch])
+    assert len(grids) == len(batch)
+    for s, g in zip(batch, grids):
+        o = oracle.build_grid(s.verts, s.tris, s.lam, method="alg1" if s.n < 50_000 else "counting")
+        assert_grid_equal(g, o, f"batched {s.name}")
+        if s.n:
+            p = ctx.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+            assert torch.equal(p.cells, g.cells) and torch.equal(p.refs, g.refs), s.name
+
+
+def test_batched_twice_same_result(ctx):
+    batch = _mixed_batch()
+    args = [(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam) for s in batch]
+    a = ctx.build_batched(args)
+    b = ctx.build_batched(args)
+    for x, y in zip(a, b):
+        assert torch.equal(x.cells, y.cells) and torch.equal(x.refs, y.refs)
+
+
+def test_batched_rejects_bad_mesh(ctx):
+    import paper_2403_10647_gb300 as pg
+    s = scenes.uniform_soup(1000, seed=5)
+    bad = s.tris.copy()
+    bad[10, 0] = s.verts.shape[0] + 3
+    with pytest.raises(pg.GridError) as e:
+        ctx.build_batched([(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam),
+                           (dev(s.verts, torch.float32), dev(bad, torch.int32), s.lam)])
+    assert e.value.code == -1
+
+
+@pytest.mark.slow
+def test_batched_64_meshes_match_plain(ctx):
+    """The 64-mesh batch (sizes log-uniform in [1e3, 2e6]) against 64 plain
+    builds, mesh by mesh, and against the oracle on a spread of meshes."""
+    meshes = scenes.batched_meshes()
+    args = [(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam) for s in meshes]
+    grids = ctx.build_batched(args)
+    order = np.argsort([s.n for s in meshes])
+    check_oracle = set(order[:3].tolist()) | set(order[len(order) // 2: len(order) // 2 + 2].tolist()) | {int(order[-1])}
+    for k, (s, g, a) in enumerate(zip(meshes, grids, args)):
+        p = ctx.build(*a)
+        assert torch.equal(p.cells, g.cells) and torch.equal(p.refs, g.refs), k
+        if k in check_oracle:
+            assert_grid_equal(g, oracle.build_grid(s.verts, s.tris, s.lam, method="counting"), f"mesh {k}")
+        del p
