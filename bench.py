@@ -7,6 +7,17 @@ resident in HBM before timing.  One step = one whole BuildParallelGrid
 (bounds, CountCells + ExclusiveSum, pair generation, radix sort, ranges)
 through the C ABI.  Prints one JSON line.
 
+At one GPU the line also carries (unless --no-extras):
+  batched, batched_small  64 meshes (triangle counts log-uniform in [1e3, 2e6],
+                          and the same x 0.01) in one grid_build_batched
+                          against 64 back-to-back grid_build calls;
+  serve                   the rebuild-serving loop on a pool of 12 registered
+                          meshes (1e4 .. 1e7 triangles) with per-request
+                          jitter: Poisson arrivals (--serve-rate per s for
+                          --serve-seconds) with p50 / p99 latency, and a
+                          saturated run against the same requests built back
+                          to back.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With N > 1 (torchrun) every rank builds its own grid (independent problems:
@@ -39,6 +50,10 @@ def parse():
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-build and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -174,6 +189,147 @@ def run_reference(args, rank, world):
     }))
 
 
+def bench_batched(ctx, scale: float, reps: int = 5):
+    """Many meshes at once: one grid_build_batched against the same meshes
+    built back to back with grid_build, identical outputs checked."""
+    import torch
+    import scenes
+    meshes = scenes.batched_meshes(64, scale=scale)
+    args = [(torch.from_numpy(s.verts).cuda(), torch.from_numpy(s.tris).cuda(), s.lam) for s in meshes]
+    torch.cuda.synchronize()
+    batched = ctx.build_batched(args)
+    for a, b in zip(args, batched):
+        p = ctx.build(*a)
+        assert torch.equal(p.cells, b.cells) and torch.equal(p.refs, b.refs), "batched != plain"
+    pairs = int(sum(b.info.nrefs for b in batched))
+    del batched, p
+    for _ in range(2):
+        ctx.build_batched(args)
+        for a in args:
+            ctx.build(*a)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g = ctx.build_batched(args)
+        del g
+    torch.cuda.synchronize()
+    tb = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for a in args:
+            g = ctx.build(*a)
+            del g
+    torch.cuda.synchronize()
+    tp = (time.perf_counter() - t0) / reps
+    return {"meshes": len(meshes), "tris": int(sum(s.n for s in meshes)), "pairs": pairs,
+            "mesh_tris": [int(min(s.n for s in meshes)), int(max(s.n for s in meshes))],
+            "batched_ms": tb * 1e3, "plain_back_to_back_ms": tp * 1e3,
+            "batched_builds_per_s": len(meshes) / tb, "plain_builds_per_s": len(meshes) / tp,
+            "speedup": tp / tb, "reps": reps, "outputs": "identical (checked)"}
+
+
+def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 4, max_batch: int = 32):
+    """The rebuild-serving loop: a pool of registered meshes, requests with
+    per-request jitter (sigma 0.01).  (1) open loop: Poisson arrivals at
+    `rate` for `seconds`, latency percentiles; (2) saturated: the first 1000
+    requests offered as fast as admission allows, builds/s against the same
+    requests built back to back (jitter + grid_build on one stream)."""
+    import queue
+    import threading
+    import torch
+    import scenes
+    import paper_2403_10647_gb300 as pg
+    pool = scenes.serving_pool()
+    arr, mesh, seeds = scenes.poisson_requests(rate, seconds, len(pool))
+    sigma = 0.01
+    srv = pg.Server(0, nworkers=nworkers, max_batch=max_batch)
+    try:
+        ids = [srv.register(s.verts, s.tris, s.lam) for s in pool]
+        # warm every worker and mesh once
+        for tk in [srv.submit(ids[k], sigma, k) for k in range(len(pool)) for _ in range(2)]:
+            srv.wait(tk).release()
+        srv.stats(reset=True)
+
+        def collect(q):
+            while True:
+                tk = q.get()
+                if tk is None:
+                    return
+                srv.wait(tk).release()
+
+        # (1) open loop
+        q = queue.Queue()
+        th = threading.Thread(target=collect, args=(q,))
+        th.start()
+        refused = 0
+        t0 = time.perf_counter()
+        for ta, m, sd in zip(arr, mesh, seeds):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tk = srv.submit(ids[int(m)], sigma, int(sd))
+            if tk is None:
+                refused += 1
+                continue
+            q.put(tk)
+        q.put(None)
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats(reset=True)
+        open_loop = {"rate_per_s": rate, "seconds": seconds, "requests": int(len(arr)),
+                     "completed": st["completed"], "failed": st["failed"], "refused": st["refused"],
+                     "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3,
+                     "max_ms": st["max_us"] / 1e3, "p50_service_ms": st["p50_service_us"] / 1e3,
+                     "builds_per_s": st["completed"] / wall, "batches": st["batches"],
+                     "batched_requests": st["batched_requests"],
+                     "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9, "budget_gb": st["budget_bytes"] / 1e9}
+
+        # (2) saturated, against back to back
+        nsat = min(1000, len(arr))
+        reqs = [(int(m), int(sd)) for m, sd in zip(mesh[:nsat], seeds[:nsat])]
+        pending = []
+        t0 = time.perf_counter()
+        for m, sd in reqs:
+            while True:
+                tk = srv.submit(ids[m], sigma, sd)
+                if tk is not None:
+                    pending.append(tk)
+                    break
+                if not pending:
+                    raise RuntimeError("one request exceeds the serving memory budget")
+                srv.wait(pending.pop(0)).release()
+        for tk in pending:
+            srv.wait(tk).release()
+        sat_wall = time.perf_counter() - t0
+        st = srv.stats(reset=True)
+        # spot-check identical outputs: every 50th request served vs plain
+        dev = [(torch.from_numpy(s.verts).cuda(), torch.from_numpy(s.tris).cuda(), s.lam) for s in pool]
+        for m, sd in reqs[::50]:
+            r = srv.wait(srv.submit(ids[m], sigma, sd))
+            v, t, lam = dev[m]
+            p = ctx.build(ctx.jitter(v, sigma, sd), t, lam)
+            assert torch.equal(p.cells, r.cells) and torch.equal(p.refs, r.refs), "served != plain"
+            r.release()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for m, sd in reqs:
+            v, t, lam = dev[m]
+            g = ctx.build(ctx.jitter(v, sigma, sd), t, lam)
+            del g
+        torch.cuda.synchronize()
+        b2b_wall = time.perf_counter() - t0
+        saturated = {"requests": nsat, "builds_per_s": nsat / sat_wall, "p50_ms": st["p50_us"] / 1e3,
+                     "p99_ms": st["p99_us"] / 1e3, "batches": st["batches"],
+                     "batched_requests": st["batched_requests"],
+                     "back_to_back_builds_per_s": nsat / b2b_wall,
+                     "speedup": (nsat / sat_wall) / (nsat / b2b_wall), "outputs": "identical (every 50th checked)"}
+    finally:
+        srv.close()
+    return {"pool_meshes": len(pool), "pool_tris": [int(min(s.n for s in pool)), int(max(s.n for s in pool))],
+            "sigma": sigma, "workers": nworkers, "max_batch": max_batch,
+            "open_loop": open_loop, "saturated": saturated}
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -281,6 +437,12 @@ def run_ours(args, rank, world, local):
                "sample": f"whole {WORKLOAD} ({ntri} triangles, {nr} pairs), counting placement, "
                          f"single-threaded C, {dt:.1f} s"}
 
+    extras = {}
+    if not args.no_extras and world == 1:
+        extras["batched"] = bench_batched(ctx, 1.0)
+        extras["batched_small"] = bench_batched(ctx, 0.01, reps=20)
+        extras["serve"] = bench_serve(ctx, args.serve_seconds, args.serve_rate)
+
     launches = int(sum(s["launches"] for s in stats.values()))
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -294,6 +456,7 @@ def run_ours(args, rank, world, local):
         "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(),
     }
+    out.update(extras)
     print(json.dumps(out))
     ctx.close()
     if dist is not None:

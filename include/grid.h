@@ -224,6 +224,103 @@ int grid_sort_pairs(grid_ctx *ctx, const int32_t *C, const int32_t *O, int64_t c
 int grid_extract_ranges(grid_ctx *ctx, const int32_t *C_sorted, int64_t count, int64_t ncells,
                         int32_t *cells);
 
+/* ---- per-request vertex jitter ------------------------------------------- */
+
+/* Not a step of the method: the perturbation the serving loop applies to a
+ * registered mesh before each rebuild (a moving scene).  out[e] = verts[e] +
+ * d(e) for the 3 * nverts floats e, where d(e) = n(e) * (sigma * sqrt(3))
+ * with the factor rounded to float once and n(e) = ((u0 + u1) + (u2 + u3)) -
+ * 2, u_k = (x_k >> 8) * 2^-24 and (x_0..x_3) = Philox4x32-10 (Salmon et al.,
+ * SC'11) of counter (e / 3, e % 3, 0, 0) under key (seed & 0xffffffff,
+ * seed >> 32).  Every operation is one float32 add or multiply rounded to
+ * nearest, so a host implementation of the same definition gives the same
+ * bits.  n has mean 0, variance 1/3 * 3 = 1, and |n| <= 2.  verts and out
+ * (float32 [nverts][3]) are device pointers; out may equal verts.
+ * GRID_EINVAL for negative nverts, NULL pointers with nverts > 0, or sigma
+ * negative or non-finite.  Enqueued on the context's stream; does not
+ * synchronise. */
+int grid_jitter(grid_ctx *ctx, const float *verts, float *out, int64_t nverts, float sigma, uint64_t seed);
+
+/* ---- rebuild-serving loop --------------------------------------------------- */
+
+/* A server keeps registered meshes resident on one GPU and rebuilds them on
+ * request: each request names a mesh, a jitter sigma and a seed; the server
+ * jitters the mesh's vertices on the device (grid_jitter's definition) and
+ * builds its grid with Algorithm 1.  Worker threads, each with its own
+ * stream and context, take queued requests in arrival order; a free worker
+ * takes every queued request up to max_batch (and up to batch_pairs estimated
+ * pairs) and builds them as one batch (grid_build_batched; grid_build for a
+ * batch of one).  A request's result is bit-identical whichever batch,
+ * worker or stream builds it.
+ *
+ * Admission: every admitted request reserves an estimate of the device bytes
+ * its rebuild needs (outputs plus scratch, from the mesh's pair and cell
+ * counts measured at registration, with 10% headroom) until it is released;
+ * grid_serve_submit refuses with GRID_EAGAIN when the reservations would pass
+ * hbm_budget. */
+typedef struct grid_server grid_server;
+
+typedef struct {
+    int32_t nworkers;     /* worker threads / streams; 0 -> 4 */
+    int32_t max_batch;    /* requests per batched build; 0 -> 32 */
+    int64_t batch_pairs;  /* cap on a batch's estimated pairs (a larger single request runs alone);
+                             0 -> 2^27 */
+    int64_t hbm_budget;   /* bytes that admitted requests may reserve; 0 -> 3/4 of the device's free
+                             memory when the server is created */
+    int32_t radix_bits;   /* as grid_opts.radix_bits; 0 -> default */
+    int32_t reserved[5];
+} grid_serve_opts;
+
+typedef struct {
+    int64_t submitted;    /* admitted requests */
+    int64_t completed;    /* finished (successfully or not) */
+    int64_t failed;       /* finished with an error */
+    int64_t refused;      /* GRID_EAGAIN answers */
+    int64_t batches;      /* builds run (a batch of one counts) */
+    int64_t batched_requests;  /* requests built in batches of two or more */
+    int64_t queued;       /* waiting for a worker now */
+    int64_t reserved_bytes;     /* admission reservations now */
+    int64_t peak_reserved_bytes;
+    int64_t budget_bytes;
+    double p50_us, p99_us, mean_us, max_us;   /* latency, submit -> result ready */
+    double p50_service_us;      /* build time of a request's batch, median */
+    double builds_per_s;        /* completed / (last completion - first submission) */
+    double elapsed_s;           /* that interval */
+} grid_serve_stats;
+
+/* Starts a server on CUDA device `device`; opts may be NULL. */
+int grid_serve_create(int device, const grid_serve_opts *opts, grid_server **out);
+/* Stops the workers after their current batch, drops queued requests and
+ * frees every result and registered mesh. */
+void grid_serve_destroy(grid_server *srv);
+/* Copies a mesh (verts float32 [nverts][3], tris int32 [n][3]; host or device
+ * pointers) into server-owned device memory, validates it with one build at
+ * `lambda` and measures its pair and cell counts for admission.  Errors as
+ * grid_build.  Synchronous; safe to call while requests run. */
+int grid_serve_register(grid_server *srv, const float *verts, int64_t nverts, const int32_t *tris,
+                        int64_t n, float lambda, int32_t *mesh_id);
+/* Queues a rebuild of mesh_id with jitter sigma (>= 0; 0 = the registered
+ * vertices) and seed; *ticket identifies it.  GRID_EAGAIN when admission
+ * refuses (nothing queued), GRID_EINVAL for an unknown mesh or bad sigma. */
+int grid_serve_submit(grid_server *srv, int32_t mesh_id, float sigma, uint64_t seed, uint64_t *ticket);
+/* If the request has finished: GRID_OK with views of its result (device
+ * pointers owned by the server, valid until grid_serve_release; never pass
+ * them to grid_buf_free) or the build's error code.  GRID_ENOTREADY while it
+ * is queued or running, GRID_EINVAL for an unknown or released ticket.  Any
+ * output pointer may be NULL. */
+int grid_serve_poll(grid_server *srv, uint64_t ticket, grid_buf *cells, grid_buf *refs, grid_info *info);
+/* As grid_serve_poll, waiting up to timeout_us (< 0: no limit) for the
+ * request to finish; GRID_ETIMEOUT if it has not. */
+int grid_serve_wait(grid_server *srv, uint64_t ticket, int64_t timeout_us, grid_buf *cells, grid_buf *refs,
+                    grid_info *info);
+/* Frees a finished request's result and its admission reservation.
+ * GRID_ENOTREADY while it is queued or running, GRID_EINVAL if unknown. */
+int grid_serve_release(grid_server *srv, uint64_t ticket);
+/* Counters and latency percentiles since creation or the last reset
+ * (reset != 0 clears them after copying; the gauges queued / reserved_bytes /
+ * budget_bytes are never cleared). */
+int grid_serve_get_stats(grid_server *srv, grid_serve_stats *out, int reset);
+
 /* ---- without allocation -------------------------------------------------- */
 
 /* The range extraction of grid_extract_ranges for callers that cannot

@@ -13,9 +13,9 @@ import ctypes
 import dataclasses
 
 from . import _lib
-from ._lib import GridError, GridInfo, GridBuf, GridOpts, check
+from ._lib import GridError, GridInfo, GridBuf, GridOpts, GridServeOpts, GridServeStats, check
 
-__all__ = ["Context", "Info", "Grid", "plan", "GridError"]
+__all__ = ["Context", "Server", "Info", "Grid", "plan", "GridError"]
 
 
 @dataclasses.dataclass
@@ -210,6 +210,18 @@ class Context:
         nc, nr = int(info.ncells) + 1, int(info.nrefs)
         return cells_out[:nc], refs_out[:nr], Info.from_c(info)
 
+    def jitter(self, verts, sigma: float, seed: int):
+        """Per-request vertex jitter of the serving loop (grid_jitter): a new
+        float32 [nv, 3] device tensor, verts + sigma-scaled Philox4x32-10
+        Irwin-Hall noise for request `seed`."""
+        torch = self._torch
+        v = self._dev(verts, torch.float32, 3)
+        out = torch.empty_like(v)
+        self._bind_stream()
+        check(self._lib.grid_jitter(self._h, v.data_ptr(), out.data_ptr(), v.shape[0], float(sigma),
+                                    int(seed) & 0xFFFFFFFFFFFFFFFF), "grid_jitter")
+        return out
+
     # -- steps -------------------------------------------------------------------
     def bounds(self, verts, tris):
         torch = self._torch
@@ -266,3 +278,141 @@ class Context:
         check(self._lib.grid_extract_ranges(self._h, C.data_ptr(), C.numel(), int(ncells), G.data_ptr()),
               "grid_extract_ranges")
         return G
+
+
+class _Lease:
+    """Keeps one served result alive: the cells / refs views point into
+    server-owned memory, which grid_serve_release frees once the last view is
+    dropped (or release() is called)."""
+
+    def __init__(self, server: "Server", ticket: int):
+        self._server = server
+        self.ticket = ticket
+        self.released = False
+
+    def release(self):
+        if not self.released:
+            self.released = True
+            h = getattr(self._server, "_h", None)
+            if h:
+                self._server._lib.grid_serve_release(h, self.ticket)
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class _View:
+    """A non-owning CUDA-array-interface view into a served result."""
+
+    def __init__(self, lease: _Lease, buf: GridBuf):
+        self._lease = lease
+        self.__cuda_array_interface__ = {
+            "shape": (int(buf.count),), "typestr": "<i4", "data": (int(buf.ptr or 0), False),
+            "version": 3, "strides": None, "stream": None,
+        }
+
+
+@dataclasses.dataclass
+class ServedGrid:
+    ticket: int
+    cells: "object"   # torch int32 [ncells + 1], CUDA, view into server memory
+    refs: "object"    # torch int32 [nrefs], CUDA, view into server memory
+    info: Info
+    lease: _Lease
+
+    def release(self):
+        """Frees the result now; the cells / refs views must not be used after."""
+        self.lease.release()
+
+
+class Server:
+    """Rebuild-serving loop (C: grid_server): registered meshes stay resident
+    on the device; each request rebuilds one with its own vertex jitter.
+    Worker threads with their own streams batch whatever is queued when they
+    become free; admission is by a device-memory budget."""
+
+    def __init__(self, device: int = 0, nworkers: int = 0, max_batch: int = 0, batch_pairs: int = 0,
+                 hbm_budget: int = 0, radix_bits: int = 0):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", device)
+        self._lib = _lib.load()
+        o = GridServeOpts()
+        o.nworkers, o.max_batch, o.batch_pairs = int(nworkers), int(max_batch), int(batch_pairs)
+        o.hbm_budget, o.radix_bits = int(hbm_budget), int(radix_bits)
+        h = ctypes.c_void_p()
+        check(self._lib.grid_serve_create(int(device), ctypes.byref(o), ctypes.byref(h)), "grid_serve_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            h, self._h = self._h, None
+            self._lib.grid_serve_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register(self, verts, tris, lam: float) -> int:
+        """Copies a mesh (numpy arrays or tensors, host or device) into server
+        memory; returns its mesh id."""
+        torch = self._torch
+        v = torch.as_tensor(verts, dtype=torch.float32).reshape(-1, 3).contiguous()
+        t = torch.as_tensor(tris, dtype=torch.int32).reshape(-1, 3).contiguous()
+        mid = ctypes.c_int32()
+        check(self._lib.grid_serve_register(self._h, v.data_ptr() if v.numel() else None, v.shape[0],
+                                            t.data_ptr() if t.numel() else None, t.shape[0], float(lam),
+                                            ctypes.byref(mid)), "grid_serve_register")
+        return int(mid.value)
+
+    def submit(self, mesh_id: int, sigma: float = 0.0, seed: int = 0):
+        """Queues a rebuild; returns its ticket, or None when admission refuses."""
+        tk = ctypes.c_uint64()
+        rc = self._lib.grid_serve_submit(self._h, int(mesh_id), float(sigma), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                         ctypes.byref(tk))
+        if rc == _lib.GRID_EAGAIN:
+            return None
+        check(rc, "grid_serve_submit")
+        return int(tk.value)
+
+    def _result(self, ticket, cb, rb, info) -> ServedGrid:
+        torch = self._torch
+        lease = _Lease(self, ticket)
+
+        def view(b):
+            if not b.ptr or b.count == 0:
+                return torch.zeros(int(b.count), dtype=torch.int32, device=self.device)
+            return torch.as_tensor(_View(lease, b), device=self.device)
+        return ServedGrid(ticket, view(cb), view(rb), Info.from_c(info), lease)
+
+    def poll(self, ticket: int):
+        """The finished result, or None while the request is queued or running."""
+        cb, rb, info = GridBuf(), GridBuf(), GridInfo()
+        rc = self._lib.grid_serve_poll(self._h, int(ticket), ctypes.byref(cb), ctypes.byref(rb),
+                                       ctypes.byref(info))
+        if rc == _lib.GRID_ENOTREADY:
+            return None
+        check(rc, "grid_serve_poll")
+        return self._result(int(ticket), cb, rb, info)
+
+    def wait(self, ticket: int, timeout: float | None = None) -> ServedGrid:
+        """Waits for a request (timeout in seconds; None = no limit)."""
+        cb, rb, info = GridBuf(), GridBuf(), GridInfo()
+        us = -1 if timeout is None else int(timeout * 1e6)
+        check(self._lib.grid_serve_wait(self._h, int(ticket), us, ctypes.byref(cb), ctypes.byref(rb),
+                                        ctypes.byref(info)), "grid_serve_wait")
+        return self._result(int(ticket), cb, rb, info)
+
+    def release(self, ticket: int) -> int:
+        """Frees a finished request without waiting for its views (returns the C status)."""
+        return int(self._lib.grid_serve_release(self._h, int(ticket)))
+
+    def stats(self, reset: bool = False) -> dict:
+        st = GridServeStats()
+        check(self._lib.grid_serve_get_stats(self._h, ctypes.byref(st), 1 if reset else 0), "grid_serve_get_stats")
+        return {name: getattr(st, name) for name, _ in GridServeStats._fields_}

@@ -55,6 +55,20 @@ class GridOpts(ctypes.Structure):
     _fields_ = [("radix_bits", c_int32), ("reserved", c_int32 * 7)]
 
 
+class GridServeOpts(ctypes.Structure):
+    _fields_ = [("nworkers", c_int32), ("max_batch", c_int32), ("batch_pairs", c_int64),
+                ("hbm_budget", c_int64), ("radix_bits", c_int32), ("reserved", c_int32 * 5)]
+
+
+class GridServeStats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("refused", c_int64),
+                ("batches", c_int64), ("batched_requests", c_int64), ("queued", c_int64),
+                ("reserved_bytes", c_int64), ("peak_reserved_bytes", c_int64), ("budget_bytes", c_int64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("p50_service_us", ctypes.c_double),
+                ("builds_per_s", ctypes.c_double), ("elapsed_s", ctypes.c_double)]
+
+
 # name -> (restype, argtypes); one entry per function declared in include/grid.h
 SIGNATURES = {
     "grid_ctx_create": (c_int32, [ctypes.c_int, P(GridOpts), P(c_void_p)]),
@@ -80,6 +94,15 @@ SIGNATURES = {
     "grid_sort_pairs": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p]),
     "grid_extract_ranges": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "grid_extract_ranges_noalloc": (c_int32, [c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
+    "grid_jitter": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_float, ctypes.c_uint64]),
+    "grid_serve_create": (c_int32, [ctypes.c_int, P(GridServeOpts), P(c_void_p)]),
+    "grid_serve_destroy": (None, [c_void_p]),
+    "grid_serve_register": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_float, P(c_int32)]),
+    "grid_serve_submit": (c_int32, [c_void_p, c_int32, c_float, ctypes.c_uint64, P(ctypes.c_uint64)]),
+    "grid_serve_poll": (c_int32, [c_void_p, ctypes.c_uint64, P(GridBuf), P(GridBuf), P(GridInfo)]),
+    "grid_serve_wait": (c_int32, [c_void_p, ctypes.c_uint64, c_int64, P(GridBuf), P(GridBuf), P(GridInfo)]),
+    "grid_serve_release": (c_int32, [c_void_p, ctypes.c_uint64]),
+    "grid_serve_get_stats": (c_int32, [c_void_p, P(GridServeStats), ctypes.c_int]),
 }
 
 _lib = None

@@ -1,24 +1,32 @@
 // CUDA kernels (sm_103a) of the parallel uniform-grid construction
 // (Costa, Pereira, Jorge, "Building An Efficient Grid On GPU", Algorithm 1).
 //
-//   bounds_kernel      boxes of Algorithm 1: per-triangle AABB, block-reduced
-//                      scene bounds, index / finiteness checks.
-//   count_scan_kernel  CountCells + ExclusiveSum: per-object cell box and cell
-//                      count V, single-pass decoupled look-back scan -> start
-//                      offsets and NO.
-//   tile_search_kernel first object of every pair tile (binary search).
-//   emit_kernel        MakeObjectIds + InclusiveSum (as a max-scan of object
-//                      start marks) + SegmentedExclusiveSum (rid = j - start)
-//                      + MakeCellIds (GlobalCoords): one thread per pair.
-//   hist_kernel        digit histograms of every radix-sort pass in one read
-//                      (keys generated on the fly or loaded).
-//   pass_kernel        one stable LSD radix-sort pass (RadixSort of Algorithm
-//                      1): warp-level multisplit ranking, decoupled look-back
-//                      across tiles per digit, shared-memory staged scatter.
-//                      The first pass can generate its pairs instead of
-//                      reading them, so (C, O) in object order never touch HBM.
-//   extract_kernel     RunLengthEncode + NonEmptyCells + ExclusiveSum fused as
-//                      a merge path of the sorted keys against the cell ids.
+//   bounds_kernel        boxes of Algorithm 1: per-triangle AABB, block-reduced
+//                        scene bounds, index / finiteness checks.
+//   count_scan_kernel    CountCells + ExclusiveSum: per-object cell box and cell
+//                        count V, single-pass decoupled look-back scan -> start
+//                        offsets and NO.
+//   tile_search_kernel   first object of every pair tile (binary search).
+//   emit_kernel          MakeObjectIds + InclusiveSum (as a max-scan of object
+//                        start marks) + SegmentedExclusiveSum (rid = j - start)
+//                        + MakeCellIds (GlobalCoords): the object-order lists.
+//   upsweep_kernel       per-tile digit counts of one RadixSort pass, prefixed
+//                        across groups of tiles by a decoupled look-back; the
+//                        first pass generates its pairs (the emit steps above)
+//                        instead of reading them and also histograms every
+//                        later pass.
+//   downsweep_kernel     one stable LSD radix-sort pass (RadixSort of Algorithm
+//                        1): warp multisplit ranking, shared-memory staged,
+//                        coalesced scatter.  The first pass again generates its
+//                        pairs, so (C, O) in object order never touch HBM.
+//   extract_kernel       RunLengthEncode + NonEmptyCells + ExclusiveSum fused as
+//                        a merge path of the sorted keys against the cell ids.
+//   bounds_batched_kernel, localize_kernel
+//                        the same method over a batch of meshes flattened into
+//                        one problem.
+//   jitter_kernel        per-request vertex jitter of the serving loop
+//                        (Philox4x32-10), not part of the method.
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 
@@ -1093,6 +1101,75 @@ cudaError_t launch_bounds_batched(const MeshTab &mt, long long ntot, unsigned *b
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// per-request vertex jitter (serving loop)
+// ---------------------------------------------------------------------------
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the
+// round constants 0xD2511F53 / 0xCD9E8D57, the key bumped by the Weyl
+// increments 0x9E3779B9 / 0xBB67AE85 after every round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Unit-variance normal as an Irwin-Hall sum of four 24-bit uniforms, minus
+// its mean 2 (variance 4/12, so the caller's factor is sigma * sqrt(3)).
+// Every step is one float add in round-to-nearest: the host generator of the
+// tests performs the same operations in the same order.
+__device__ __forceinline__ float irwin_hall4(uint4 x)
+{
+    const float q = 5.9604644775390625e-8f;   // 2^-24
+    const float u0 = __fmul_rn(__uint2float_rn(x.x >> 8), q);
+    const float u1 = __fmul_rn(__uint2float_rn(x.y >> 8), q);
+    const float u2 = __fmul_rn(__uint2float_rn(x.z >> 8), q);
+    const float u3 = __fmul_rn(__uint2float_rn(x.w >> 8), q);
+    return __fsub_rn(__fadd_rn(__fadd_rn(u0, u1), __fadd_rn(u2, u3)), 2.0f);
+}
+
+__global__ void __launch_bounds__(256) jitter_kernel(JitterDesc one, const JitterDesc *__restrict__ d,
+                                                     const long long *__restrict__ ebase, int nm, long long total)
+{
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < total; e += (long long)gridDim.x * 256) {
+        JitterDesc jd = one;
+        long long local = e;
+        if (d) {   // owner: the last mesh whose first element is <= e
+            int lo = 0, hi = nm - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ebase[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            jd = d[lo];
+            local = e - ebase[lo];
+        }
+        const unsigned long long i = (unsigned long long)local / 3ull;
+        const unsigned a = (unsigned)(local - 3ll * (long long)i);
+        const uint4 x = philox4x32_10(make_uint4((unsigned)i, a, 0u, 0u), (unsigned)jd.seed,
+                                      (unsigned)(jd.seed >> 32));
+        jd.dst[local] = __fadd_rn(jd.src[local], __fmul_rn(irwin_hall4(x), jd.s));
+    }
+}
+
+cudaError_t launch_jitter(const JitterDesc &one, const JitterDesc *d, const long long *ebase, int nm,
+                          long long total, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    const long long want = (total + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 4864 ? want : 4864);   // 152 SMs x 32 blocks, grid-stride beyond
+    jitter_kernel<<<blocks, 256, 0, s>>>(one, d, ebase, nm, total);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_localize(const unsigned *G, const long long *cells_off, const unsigned *pair_base, int nm,
                             long long total, unsigned *out, cudaStream_t s)
 {
@@ -1109,6 +1186,21 @@ cudaError_t launch_count_scan(const CountArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Raises a kernel's dynamic shared-memory limit once per device.  Launchers
+// run concurrently from several host threads (one per serving worker), so the
+// per-device "done" bits are atomic; a repeated call is harmless.
+template <typename K>
+cudaError_t allow_dynamic_smem(K k, size_t smem, std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    if (cudaError_t e = cudaGetDevice(&dev)) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
 cudaError_t launch_tile_search(const ObjRec *recs, long long n, unsigned tile, unsigned ntiles,
                                unsigned *tile_obj, cudaStream_t s)
 {
@@ -1123,12 +1215,8 @@ cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s)
     const unsigned tiles = (a.count + PAIR_TILE - 1) / PAIR_TILE;
     auto k = emit_kernel<PAIR_BLOCK, PAIR_TILE / PAIR_BLOCK>;
     const size_t smem = 2 * sizeof(unsigned) * padded<PAIR_TILE>();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
     k<<<tiles, PAIR_BLOCK, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -1139,12 +1227,8 @@ static cudaError_t launch_up_t(const UpArgs &a, cudaStream_t s)
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
     auto k = upsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, SRC>;
     const size_t smem = sizeof(unsigned) * ((2 + MAX_PASSES) * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
     const unsigned groups = (a.ntiles + GROUP_TILES - 1) / GROUP_TILES;
     k<<<groups, PAIR_BLOCK, smem, s>>>(a);
     return cudaGetLastError();
@@ -1156,13 +1240,9 @@ static cudaError_t launch_down_t(const DownArgs &a, unsigned ntiles, int nsm, cu
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
     auto k = downsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, IN>;
     constexpr size_t smem = down_smem_bytes<PAIR_BLOCK, ITEMS, RBITS>();
-    static bool configured = false;
     (void)nsm;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
     k<<<ntiles, PAIR_BLOCK, smem, s>>>(a, ntiles);
     return cudaGetLastError();
 }

@@ -132,6 +132,24 @@ struct ExtractArgs {
     Ctl *ctl;
 };
 
+// Per-request vertex jitter of the serving loop: dst[e] = src[e] + s * n(e)
+// for the floats e of a mesh's vertex array, n(e) a unit-variance
+// Irwin-Hall normal from Philox4x32-10 at counter (e / 3, e % 3, 0, 0) and
+// key (seed low, seed high) words.
+struct JitterDesc {
+    const float *src;
+    float *dst;
+    unsigned long long seed;
+    float s;                        // sigma * sqrt(3), rounded to float once
+    int pad;
+};
+
+// Meshes k = 0 .. nm-1 own floats [ebase[k], ebase[k + 1]) of the flattened
+// element range [0, total).  With d == nullptr, `one` is the only mesh and
+// ebase is not read.
+cudaError_t launch_jitter(const JitterDesc &one, const JitterDesc *d, const long long *ebase, int nm,
+                          long long total, cudaStream_t s);
+
 cudaError_t launch_bounds(const float *verts, long long nverts, const int *tris, long long n, Ctl *ctl,
                           int nsm, cudaStream_t s);
 // Batched: per-mesh bounds into bstate[m * 6 + (lo_inv x, y, z, hi x, y, z)].

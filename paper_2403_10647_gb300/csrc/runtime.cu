@@ -922,6 +922,21 @@ void grid_buf_free(grid_ctx *c, grid_buf *b)
     *b = grid_buf{nullptr, 0, 0};
 }
 
+int grid_jitter(grid_ctx *c, const float *verts, float *out, int64_t nverts, float sigma, uint64_t seed)
+{
+    if (!c || nverts < 0 || !std::isfinite(sigma) || sigma < 0.0f) return GRID_EINVAL;
+    if (nverts > 0 && (!verts || !out)) return GRID_EINVAL;
+    if (nverts == 0) return GRID_OK;
+    DeviceGuard g(c->device);
+    gg::JitterDesc one{};
+    one.src = verts;
+    one.dst = out;
+    one.seed = seed;
+    one.s = sigma * 1.7320508075688772f;
+    GG_CUDA(gg::launch_jitter(one, nullptr, nullptr, 1, 3 * nverts, c->stream));
+    return GRID_OK;
+}
+
 // ---- steps ------------------------------------------------------------------
 
 int grid_bounds(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *tris, int64_t n, float lo[3],

@@ -173,6 +173,42 @@ def batched_meshes(nmeshes: int = 64, seed: int = SEED_BASE + 4, lam: float = 4.
     return out
 
 
+def serving_pool(nmeshes: int = 12, seed: int = SEED_BASE + 5, lo: float = 1e4, hi: float = 1e7):
+    """Meshes a rebuild server keeps registered: N_k log-uniform in [lo, hi];
+    by a seeded coin flip either a non-homogeneous soup (box side
+    100 * cbrt(N_k / 1e6), the 1M soup's density, lambda 4) or an
+    architectural scene (building 200 x 50 x 200 scaled by cbrt(N_k / 1e7),
+    2000 * N_k / 1e7 clutter blobs, at least 4, lambda 8)."""
+    g = rng(seed)
+    sizes = np.exp(g.uniform(math.log(lo), math.log(hi), nmeshes)).astype(np.int64)
+    arch = g.random(nmeshes) < 0.5
+    out = []
+    for k, (nk, is_arch) in enumerate(zip(sizes, arch)):
+        nk = int(nk)
+        if is_arch:
+            f = (nk / 1e7) ** (1.0 / 3.0)
+            out.append(architectural(nk, seed=seed * 1000 + k, size=(200.0 * f, 50.0 * f, 200.0 * f),
+                                     nblobs=max(4, int(round(2000 * nk / 1e7)))))
+        else:
+            out.append(nonhomogeneous_soup(nk, seed=seed * 1000 + k, extent=100.0 * (nk / 1e6) ** (1.0 / 3.0)))
+    return out
+
+
+def poisson_requests(rate: float = 200.0, duration: float = 30.0, nmeshes: int = 12,
+                     seed: int = SEED_BASE + 6):
+    """A rebuild request stream: Poisson arrivals at `rate` per second for
+    `duration` seconds (exponential gaps); each request names a mesh of the
+    pool uniformly and carries its own 63-bit jitter seed.  Returns
+    (arrival times in s, mesh ids, seeds) as numpy arrays."""
+    g = rng(seed)
+    m = int(rate * duration * 1.5) + 64
+    t = np.cumsum(g.exponential(1.0 / rate, m))
+    mesh = g.integers(0, nmeshes, m)
+    seeds = g.integers(0, 2**63, m, dtype=np.int64)
+    keep = t < duration
+    return t[keep], mesh[keep], seeds[keep]
+
+
 def tiny_scene(g: np.random.Generator, n: int, nverts: int | None = None,
                box: float = 1.0, max_edge: float = 0.5) -> Scene:
     """A small random indexed mesh for exhaustive checks: ``nverts`` vertices
@@ -191,3 +227,57 @@ CONFIGS = {
     "nonhomogeneous_1e6": lambda: nonhomogeneous_soup(),
     "architectural_1e7": lambda: architectural(),
 }
+
+
+# ---- per-request vertex jitter ------------------------------------------------------
+#
+# Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy
+# as 1, 2, 3", SC'11): a counter-based generator, written here from its
+# published definition so the CUDA side (its own implementation) can draw the
+# same numbers.  A vertex coordinate's jitter is an Irwin-Hall sum of four
+# uniforms, rescaled to unit variance: n = ((u0 + u1) + (u2 + u3)) - 2 with
+# u_k = (x_k >> 8) * 2^-24, then delta = n * s where s = sigma * sqrt(3) is
+# rounded to float32 once; every operation is a single float32 add or
+# multiply, so host and device agree bit for bit.
+
+PHILOX_M0, PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+PHILOX_W0, PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Vectorised Philox4x32-10 on uint32 arrays (counters) and keys."""
+    M = np.uint64(0xFFFFFFFF)
+    c0, c1, c2, c3 = (np.asarray(x, np.uint64) & M for x in (c0, c1, c2, c3))
+    k0 = np.uint64(k0) & M
+    k1 = np.uint64(k1) & M
+    for _ in range(10):
+        p0 = np.uint64(PHILOX_M0) * c0
+        p1 = np.uint64(PHILOX_M1) * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & M
+        hi1, lo1 = p1 >> np.uint64(32), p1 & M
+        c0, c1, c2, c3 = (hi1 ^ c1 ^ k0) & M, lo1, (hi0 ^ c3 ^ k1) & M, lo0
+        k0 = (k0 + np.uint64(PHILOX_W0)) & M
+        k1 = (k1 + np.uint64(PHILOX_W1)) & M
+    return tuple(x.astype(np.uint32) for x in (c0, c1, c2, c3))
+
+
+def jitter_scale(sigma: float) -> np.float32:
+    """The float32 factor s = sigma * sqrt(3) both sides use."""
+    return np.float32(np.float32(sigma) * np.float32(1.7320508075688772))
+
+
+def jitter_vertices(verts: np.ndarray, sigma: float, seed: int) -> np.ndarray:
+    """verts + per-coordinate jitter of standard deviation sigma for request
+    `seed`: coordinate a of vertex i uses counter (i, a, 0, 0) and key
+    (seed & 0xffffffff, seed >> 32)."""
+    v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+    nv = v.shape[0]
+    i = np.repeat(np.arange(nv, dtype=np.uint64), 3)
+    a = np.tile(np.arange(3, dtype=np.uint64), nv)
+    zero = np.zeros_like(i)
+    x = philox4x32_10(i, a, zero, zero, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    two24 = np.float32(1.0 / 16777216.0)
+    u = [((xk >> np.uint32(8)).astype(np.float32) * two24).astype(np.float32) for xk in x]
+    n = ((u[0] + u[1]).astype(np.float32) + (u[2] + u[3]).astype(np.float32)).astype(np.float32) - np.float32(2.0)
+    d = (n.astype(np.float32) * jitter_scale(sigma)).astype(np.float32)
+    return (v.reshape(-1) + d).astype(np.float32).reshape(-1, 3)

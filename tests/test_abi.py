@@ -93,7 +93,49 @@ def test_null_arguments_rejected(lib):
     assert lib.grid_ctx_create(0, None, None) == _lib.GRID_EINVAL
 
 
-def test_struct_sizes():
-    assert ctypes.sizeof(_lib.GridInfo) == 80
-    assert ctypes.sizeof(_lib.GridBuf) == 24
-    assert ctypes.sizeof(_lib.GridOpts) == 32
+def test_null_arguments_rejected_serving(lib):
+    tk = ctypes.c_uint64()
+    assert lib.grid_serve_create(0, None, None) == _lib.GRID_EINVAL
+    assert lib.grid_serve_submit(None, 0, 0.0, 0, ctypes.byref(tk)) == _lib.GRID_EINVAL
+    assert lib.grid_serve_poll(None, 1, None, None, None) == _lib.GRID_EINVAL
+    assert lib.grid_serve_wait(None, 1, 0, None, None, None) == _lib.GRID_EINVAL
+    assert lib.grid_serve_release(None, 1) == _lib.GRID_EINVAL
+    assert lib.grid_serve_get_stats(None, None, 0) == _lib.GRID_EINVAL
+    mid = ctypes.c_int32()
+    assert lib.grid_serve_register(None, None, 0, None, 0, 1.0, ctypes.byref(mid)) == _lib.GRID_EINVAL
+    assert lib.grid_jitter(None, None, None, 0, 0.01, 0) == _lib.GRID_EINVAL
+    lib.grid_serve_destroy(None)
+
+
+# (ctypes mirror, C type name, fields) of every struct the ABI passes by pointer
+_STRUCTS = [
+    (_lib.GridInfo, "grid_info"), (_lib.GridBuf, "grid_buf"), (_lib.GridOpts, "grid_opts"),
+    (_lib.GridMesh, "grid_mesh"), (_lib.GridKernelStat, "grid_kernel_stat"),
+    (_lib.GridServeOpts, "grid_serve_opts"), (_lib.GridServeStats, "grid_serve_stats"),
+]
+# ctypes field names that differ from the header's
+_RENAMED = {("grid_mesh", "lam"): "lambda"}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """sizeof and every field offset of the ctypes mirrors equal what a C
+    compiler makes of include/grid.h."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "grid.h"', 'int main(void) {']
+    want = []
+    for cls, cname in _STRUCTS:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            cf = _RENAMED.get((cname, fname), fname)
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {cf}));')
+            want.append(getattr(cls, fname).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == want

@@ -1,0 +1,280 @@
+"""The rebuild-serving loop (grid_serve_*) and its device jitter, through the
+C ABI: the device jitter equals the host generator bit for bit, every served
+result equals the oracle's grid of the jittered mesh, a request's result is
+the same whether it is built alone or in a mix (other requests, batches,
+workers, streams), admission refuses past the memory budget, and one failing
+request does not fail the others of its batch."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def assert_same_as_oracle(res, o, what=""):
+    info = res.info
+    assert tuple(info.res) == tuple(o.plan.res), what
+    assert np.array_equal(np.array(info.lo, np.float32), o.plan.lo), what
+    assert np.array_equal(np.array(info.hi, np.float32), o.plan.hi), what
+    assert info.ncells == o.plan.ncells and info.nrefs == o.NO, what
+    assert np.array_equal(host(res.cells), o.G), (what, "cells")
+    assert np.array_equal(host(res.refs), o.refs), (what, "refs")
+
+
+# ---- device jitter ---------------------------------------------------------------
+
+@pytest.mark.parametrize("nverts,sigma,seed", [
+    (1, 0.01, 0), (7, 0.01, 1), (100_003, 0.01, 12345), (100_003, 0.5, (1 << 40) + 17),
+    (5_000, 0.0, 3), (2_000_000, 0.01, 2**64 - 1),
+])
+def test_device_jitter_matches_host(ctx, nverts, sigma, seed):
+    g = np.random.Generator(np.random.Philox(nverts))
+    v = (g.random((nverts, 3)) * 100.0 - 20.0).astype(np.float32)
+    got = host(ctx.jitter(dev(v, torch.float32), sigma, seed))
+    want = scenes.jitter_vertices(v, sigma, seed)
+    bad = np.flatnonzero(got.view(np.uint32).ravel() != want.view(np.uint32).ravel())
+    assert bad.size == 0, (bad[:8], got.ravel()[bad[:8]], want.ravel()[bad[:8]])
+
+
+def test_device_jitter_in_place(ctx):
+    v = scenes.uniform_soup(3000, seed=8).verts
+    t = dev(v, torch.float32)
+    want = host(ctx.jitter(t, 0.02, 99))
+    ctx.jitter(t, 0.02, 99)   # out == verts is allowed
+    assert np.array_equal(host(ctx.jitter(dev(v, torch.float32), 0.02, 99)), want)
+
+
+# ---- serving -----------------------------------------------------------------------
+
+def _pool():
+    g = np.random.Generator(np.random.Philox(777))
+    return [
+        scenes.uniform_soup(4_000, seed=301),
+        scenes.nonhomogeneous_soup(12_000, seed=302, extent=20.0),
+        scenes.architectural(20_000, seed=303, size=(25.0, 6.0, 25.0), nblobs=15),
+        scenes.tiny_scene(g, 23),
+        scenes.nonhomogeneous_soup(250_000, seed=304, extent=60.0),
+    ]
+
+
+def _requests(nreq, nmesh, seed=55):
+    g = np.random.Generator(np.random.Philox(seed))
+    mesh = g.integers(0, nmesh, nreq)
+    sig = np.where(g.random(nreq) < 0.15, 0.0, 0.01)
+    seeds = g.integers(0, 2**63, nreq)
+    return [(int(m), float(s), int(sd)) for m, s, sd in zip(mesh, sig, seeds)]
+
+
+def _serve_all(srv, ids, reqs, serial):
+    """Results of every request as host arrays.  serial: submit, wait and
+    release one at a time; else submit all first, then collect."""
+    out = []
+    if serial:
+        for m, s, sd in reqs:
+            tk = srv.submit(ids[m], s, sd)
+            assert tk is not None
+            r = srv.wait(tk, timeout=120)
+            out.append((host(r.cells), host(r.refs), r.info))
+            r.release()
+        return out
+    tickets = []
+    for m, s, sd in reqs:
+        tk = srv.submit(ids[m], s, sd)
+        assert tk is not None
+        tickets.append(tk)
+    for tk in tickets:
+        r = srv.wait(tk, timeout=120)
+        out.append((host(r.cells), host(r.refs), r.info))
+        r.release()
+    return out
+
+
+@pytest.fixture(scope="module")
+def pool():
+    return _pool()
+
+
+def test_served_results_match_oracle(ctx, pool):
+    import paper_2403_10647_gb300 as pg
+    srv = pg.Server(0, nworkers=2, max_batch=4)
+    try:
+        ids = [srv.register(s.verts, s.tris, s.lam) for s in pool]
+        reqs = [(0, 0.01, 11), (1, 0.01, 12), (2, 0.01, 13), (3, 0.01, 14), (1, 0.0, 0), (4, 0.01, 2**40 + 3)]
+        tickets = [srv.submit(ids[m], s, sd) for m, s, sd in reqs]
+        for (m, s, sd), tk in zip(reqs, tickets):
+            r = srv.wait(tk, timeout=120)
+            sc = pool[m]
+            v = scenes.jitter_vertices(sc.verts, s, sd)
+            o = oracle.build_grid(v, sc.tris, sc.lam, method="alg1" if sc.n < 50_000 else "counting")
+            assert_same_as_oracle(r, o, f"mesh {m} sigma {s} seed {sd}")
+            r.release()
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["failed"] == 0
+        assert st["reserved_bytes"] == 0
+    finally:
+        srv.close()
+
+
+def test_alone_equals_in_mix(ctx, pool):
+    """Each request's result is bit-identical built alone (one worker, batches
+    of one, one request in flight) and in a mix (four workers on four
+    streams, batches of up to eight, everything queued at once)."""
+    import paper_2403_10647_gb300 as pg
+    reqs = _requests(48, len(pool))
+    alone_srv = pg.Server(0, nworkers=1, max_batch=1)
+    try:
+        ids = [alone_srv.register(s.verts, s.tris, s.lam) for s in pool]
+        alone = _serve_all(alone_srv, ids, reqs, serial=True)
+        assert alone_srv.stats()["batched_requests"] == 0
+    finally:
+        alone_srv.close()
+    mix_srv = pg.Server(0, nworkers=4, max_batch=8)
+    try:
+        ids = [mix_srv.register(s.verts, s.tris, s.lam) for s in pool]
+        mixed = _serve_all(mix_srv, ids, reqs, serial=False)
+        st = mix_srv.stats()
+    finally:
+        mix_srv.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    for k, ((ca, ra, ia), (cb, rb, ib)) in enumerate(zip(alone, mixed)):
+        assert ia == ib, k
+        assert np.array_equal(ca, cb) and np.array_equal(ra, rb), f"request {k} differs in the mix"
+
+
+def test_batches_form_behind_a_busy_worker(ctx, pool):
+    """One worker busy with a large rebuild: the requests queued meanwhile
+    are taken together as one batch, and still match the oracle."""
+    import paper_2403_10647_gb300 as pg
+    big = scenes.nonhomogeneous_soup(1_000_000, seed=305)
+    srv = pg.Server(0, nworkers=1, max_batch=16)
+    try:
+        bid = srv.register(big.verts, big.tris, big.lam)
+        ids = [srv.register(s.verts, s.tris, s.lam) for s in pool[:4]]
+        t0 = srv.submit(bid, 0.01, 1)
+        small = [(i % 4, 0.01, 1000 + i) for i in range(12)]
+        tks = [srv.submit(ids[m], s, sd) for m, s, sd in small]
+        srv.wait(t0, timeout=120).release()
+        for (m, s, sd), tk in zip(small, tks):
+            r = srv.wait(tk, timeout=120)
+            sc = pool[m]
+            o = oracle.build_grid(scenes.jitter_vertices(sc.verts, s, sd), sc.tris, sc.lam)
+            assert_same_as_oracle(r, o, f"queued request mesh {m}")
+            r.release()
+        st = srv.stats()
+        assert st["batched_requests"] >= 2, st
+        assert st["batches"] < 1 + len(small)
+    finally:
+        srv.close()
+
+
+def test_admission_refuses_beyond_budget(ctx, pool):
+    import paper_2403_10647_gb300 as pg
+    sc = pool[4]
+    probe = pg.Server(0, nworkers=1)
+    try:
+        mid = probe.register(sc.verts, sc.tris, sc.lam)
+        tk = probe.submit(mid, 0.01, 1)
+        est = probe.stats()["reserved_bytes"]
+        probe.wait(tk, timeout=120).release()
+    finally:
+        probe.close()
+    assert est > 0
+    srv = pg.Server(0, nworkers=1, hbm_budget=int(est * 1.5))
+    try:
+        mid = srv.register(sc.verts, sc.tris, sc.lam)
+        t1 = srv.submit(mid, 0.01, 1)
+        assert t1 is not None
+        assert srv.submit(mid, 0.01, 2) is None          # a second would pass the budget
+        r = srv.wait(t1, timeout=120)
+        assert srv.submit(mid, 0.01, 3) is None          # an unreleased result still holds its share
+        r.release()
+        t3 = srv.submit(mid, 0.01, 3)
+        assert t3 is not None
+        srv.wait(t3, timeout=120).release()
+        st = srv.stats()
+        assert st["refused"] == 2 and st["completed"] == 2 and st["peak_reserved_bytes"] <= int(est * 1.5)
+    finally:
+        srv.close()
+
+
+def test_failing_request_does_not_fail_its_batch(ctx, pool):
+    """sigma = 3e38 overflows the jitter to non-finite coordinates: that
+    request fails with GRID_EINVAL, the rest of its batch still succeeds."""
+    import paper_2403_10647_gb300 as pg
+    from paper_2403_10647_gb300 import _lib
+    big = scenes.nonhomogeneous_soup(1_000_000, seed=306)
+    srv = pg.Server(0, nworkers=1, max_batch=8)
+    try:
+        bid = srv.register(big.verts, big.tris, big.lam)
+        ids = [srv.register(s.verts, s.tris, s.lam) for s in pool[:3]]
+        t0 = srv.submit(bid, 0.0, 0)                     # keeps the worker busy so the rest batch up
+        reqs = [(0, 0.01, 5), (1, 3e38, 6), (2, 0.01, 7)]
+        tks = [srv.submit(ids[m], s, sd) for m, s, sd in reqs]
+        srv.wait(t0, timeout=120).release()
+        for (m, s, sd), tk in zip(reqs, tks):
+            if s > 1.0:
+                with pytest.raises(pg.GridError) as e:
+                    srv.wait(tk, timeout=120)
+                assert e.value.code == _lib.GRID_EINVAL
+                assert srv.release(tk) == 0
+                continue
+            r = srv.wait(tk, timeout=120)
+            sc = pool[m]
+            assert_same_as_oracle(r, oracle.build_grid(scenes.jitter_vertices(sc.verts, s, sd), sc.tris, sc.lam))
+            r.release()
+        st = srv.stats()
+        assert st["failed"] == 1 and st["completed"] == 4
+    finally:
+        srv.close()
+
+
+def test_bad_tickets_and_arguments(ctx, pool):
+    import paper_2403_10647_gb300 as pg
+    from paper_2403_10647_gb300 import _lib
+    srv = pg.Server(0, nworkers=1)
+    try:
+        sc = pool[0]
+        mid = srv.register(sc.verts, sc.tris, sc.lam)
+        with pytest.raises(pg.GridError):
+            srv.wait(987654, timeout=1)
+        with pytest.raises(pg.GridError):
+            srv.submit(mid + 5, 0.01, 1)
+        with pytest.raises(pg.GridError):
+            srv.submit(mid, -1.0, 1)
+        with pytest.raises(pg.GridError):
+            srv.submit(mid, float("nan"), 1)
+        with pytest.raises(pg.GridError):   # a bad vertex index fails registration
+            srv.register(sc.verts, np.array([[0, 1, 10**6]], np.int32), 2.0)
+        tk = srv.submit(mid, 0.01, 1)
+        r = srv.wait(tk, timeout=120)
+        assert srv.poll(tk) is not None
+        r.release()
+        assert srv.release(tk) == _lib.GRID_EINVAL    # already released
+        with pytest.raises(pg.GridError):
+            srv.poll(tk)
+    finally:
+        srv.close()
+
+
+def test_empty_mesh_is_served(ctx):
+    import paper_2403_10647_gb300 as pg
+    srv = pg.Server(0, nworkers=2)
+    try:
+        mid = srv.register(np.zeros((4, 3), np.float32), np.zeros((0, 3), np.int32), 2.0)
+        r = srv.wait(srv.submit(mid, 0.01, 1), timeout=60)
+        assert host(r.cells).tolist() == [0, 0] and r.refs.numel() == 0 and tuple(r.info.res) == (1, 1, 1)
+        r.release()
+    finally:
+        srv.close()
