@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
+                    help="the scene one step builds (default: the 10M-triangle architectural scene)")
     ap.add_argument("--radix-bits", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -146,9 +148,20 @@ def traffic_from_profiles(kernel: str, nrefs: int):
     return None
 
 
-def make_scene():
+# the metric's workload, the two smaller configurations, and a 2.5M-triangle
+# architectural scene at the same density (a few GB on the device) for
+# profiler captures that replay kernels many times
+WORKLOADS = {
+    "architectural_1e7": lambda sc: sc.CONFIGS["architectural_1e7"](),
+    "nonhomogeneous_1e6": lambda sc: sc.CONFIGS["nonhomogeneous_1e6"](),
+    "uniform_1e5": lambda sc: sc.CONFIGS["uniform_1e5"](),
+    "architectural_2.5e6": lambda sc: sc.architectural_scaled(2_500_000),
+}
+
+
+def make_scene(workload: str = WORKLOAD):
     import scenes
-    return scenes.CONFIGS[WORKLOAD]()
+    return WORKLOADS[workload](scenes)
 
 
 def cpu_oracle_rate(scene, stride: int = 1):
@@ -167,7 +180,7 @@ def run_reference(args, rank, world):
     """The oracle on the host cores, as the reference arm."""
     if rank != 0:
         return
-    scene = make_scene()
+    scene = make_scene(args.workload)
     stride = 10
     for _ in range(args.warmup):
         cpu_oracle_rate(scene, stride)
@@ -178,12 +191,12 @@ def run_reference(args, rank, world):
         secs.append(dt)
     tot = sum(secs)
     value = nrefs * args.steps / tot
-    sample = f"every {stride}th triangle of {WORKLOAD} ({ntri} triangles, {nrefs} pairs) per step"
+    sample = f"every {stride}th triangle of {args.workload} ({ntri} triangles, {nrefs} pairs) per step"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_stride": stride},
+        "data": "synthetic", "config": {"workload": args.workload, "sample_stride": stride},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -226,6 +239,53 @@ def bench_batched(ctx, scale: float, reps: int = 5):
             "batched_ms": tb * 1e3, "plain_back_to_back_ms": tp * 1e3,
             "batched_builds_per_s": len(meshes) / tb, "plain_builds_per_s": len(meshes) / tp,
             "speedup": tp / tb, "reps": reps, "outputs": "identical (checked)"}
+
+
+def bench_pair_gen(scene, reps: int = 5):
+    """Pair-generation ablation on one scene: the default fused path (pairs
+    generated inside the first sort pass), the paper's unfused chain (pairs
+    written to device memory by one thread per pair, then sorted) and the
+    sorted grid's one-thread-per-object MakePairs, each timed per build with
+    CUDA events and per kernel with the library's own event accounting."""
+    import torch
+    import paper_2403_10647_gb300 as pg
+    v = torch.from_numpy(scene.verts).cuda()
+    t = torch.from_numpy(scene.tris).cuda()
+    out = {"n_tris": scene.n}
+    ref = None
+    for mode in ("fused", "emit", "per_object"):
+        c = pg.Context(0, pair_gen=mode)
+        try:
+            g = c.build(v, t, scene.lam)
+            if ref is None:
+                ref = g
+                out["nrefs"] = g.info.nrefs
+            else:
+                assert torch.equal(ref.cells, g.cells) and torch.equal(ref.refs, g.refs), mode
+            del g
+            for _ in range(2):
+                c.build(v, t, scene.lam)
+            c.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                g = c.build(v, t, scene.lam)
+                del g
+            e1.record()
+            torch.cuda.synchronize()
+            st = c.kernel_stats()
+            c.profile(False)
+            gen = {"fused": ("upsweep_gen", "downsweep_gen"), "emit": ("tile_search", "emit"),
+                   "per_object": ("make_pairs_per_object",)}[mode]
+            out[mode] = {"ms_per_build": e0.elapsed_time(e1) / reps,
+                         "pair_generation_ms": sum(st[k]["ms"] for k in gen if k in st) / reps,
+                         "pair_generation_kernels": list(gen)}
+        finally:
+            c.close()
+    del ref
+    out["outputs"] = "identical in every mode (checked)"
+    return out
 
 
 def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 4, max_batch: int = 32):
@@ -345,7 +405,7 @@ def run_ours(args, rank, world, local):
         if dist is not None:
             dist.barrier()
 
-    scene = make_scene()
+    scene = make_scene(args.workload)
     ctx = pg.Context(local, radix_bits=args.radix_bits)
     v = torch.from_numpy(scene.verts).cuda()
     t = torch.from_numpy(scene.tris).cuda()
@@ -434,7 +494,7 @@ def run_ours(args, rank, world, local):
     if not args.no_cpu_baseline and world == 1:
         rate, dt, ntri, nr = cpu_oracle_rate(scene, 1)
         cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-               "sample": f"whole {WORKLOAD} ({ntri} triangles, {nr} pairs), counting placement, "
+               "sample": f"whole {args.workload} ({ntri} triangles, {nr} pairs), counting placement, "
                          f"single-threaded C, {dt:.1f} s"}
 
     extras = {}
@@ -442,15 +502,21 @@ def run_ours(args, rank, world, local):
         extras["batched"] = bench_batched(ctx, 1.0)
         extras["batched_small"] = bench_batched(ctx, 0.01, reps=20)
         extras["serve"] = bench_serve(ctx, args.serve_seconds, args.serve_rate)
+        extras["pair_gen_ablation"] = {args.workload: bench_pair_gen(scene)}
+        if args.workload != "nonhomogeneous_1e6":
+            extras["pair_gen_ablation"]["nonhomogeneous_1e6"] = bench_pair_gen(make_scene("nonhomogeneous_1e6"))
 
+    in_mb = (scene.verts.nbytes + scene.tris.nbytes) / 1e6
+    l2_note = (f"inputs larger than L2 ({in_mb:.0f} MB)" if in_mb > 129 else
+               f"inputs {in_mb:.0f} MB; pair arrays {8 * nrefs / 1e6:.0f} MB")
     launches = int(sum(s["launches"] for s in stats.values()))
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_tris": scene.n, "lambda": scene.lam, "grid": list(info.res),
+        "config": {"workload": args.workload, "n_tris": scene.n, "lambda": scene.lam, "grid": list(info.res),
                    "ncells": info.ncells, "nrefs": nrefs, "key_bits": info.key_bits,
-                   "radix_bits": args.radix_bits or 9, "l2": "inputs larger than L2 (474 MB)",
+                   "radix_bits": args.radix_bits or 9, "l2": l2_note,
                    "parallelism": f"replicas{world}"},
         "builds_per_s": world * args.steps / (ms_max / 1e3),
         "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,

@@ -90,10 +90,20 @@ typedef struct {
     uint32_t start;       /* exclusive prefix sum of the cell counts V */
 } grid_objrec;
 
+/* How grid_build produces the object-order pairs (C, O) of MakeObjectIds ..
+ * MakeCellIds.  The pairs, and so the grid, are the same in every mode. */
+#define GRID_PAIRS_FUSED 0       /* one thread per pair, inside the first radix-sort pass; (C, O)
+                                    never reach device memory (default) */
+#define GRID_PAIRS_EMIT 1        /* one thread per pair, written to device memory, then sorted
+                                    (the paper's chain of separate steps) */
+#define GRID_PAIRS_PER_OBJECT 2  /* ablation: one thread per object writes all its pairs (the
+                                    sorted grid's MakePairs, Sec. 2), then sorted */
+
 /* Tuning knobs; zero means "library default / autotuned". */
 typedef struct {
     int32_t radix_bits;   /* widest digit of the LSD radix sort: 8..11 (default 9) */
-    int32_t reserved[7];
+    int32_t pair_gen;     /* GRID_PAIRS_*; single-mesh builds only (batched builds always fuse) */
+    int32_t reserved[6];
 } grid_opts;
 
 /* ---- context -------------------------------------------------------------- */
@@ -210,6 +220,12 @@ int grid_count_scan(grid_ctx *ctx, const float *verts, int64_t nverts, const int
  * object-order lists C (cell id) and O (object id), int32 [nrefs] each. */
 int grid_emit_pairs(grid_ctx *ctx, const grid_objrec *recs, int64_t n, int64_t nrefs,
                     const grid_info *info, int32_t *C, int32_t *O);
+
+/* The same object-order lists as grid_emit_pairs, written by one thread per
+ * object (the sorted grid's MakePairs, Sec. 2): an ablation of the pair
+ * generation, not a step of Algorithm 1.  Same arguments and result. */
+int grid_emit_pairs_per_object(grid_ctx *ctx, const grid_objrec *recs, int64_t n, int64_t nrefs,
+                               const grid_info *info, int32_t *C, int32_t *O);
 
 /* a8, RadixSort(C, O) (Algorithm 1, Fig. 4c): stable LSD sort of the pairs by
  * the low key_bits bits of C (0..31; keys must be < 2^key_bits).  Writes

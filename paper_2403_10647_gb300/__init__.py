@@ -82,13 +82,17 @@ class _LibBuffer:
 class Context:
     """A grid-builder context on one CUDA device (C: grid_ctx)."""
 
-    def __init__(self, device: int = 0, radix_bits: int = 0):
+    PAIR_GEN = {"fused": _lib.GRID_PAIRS_FUSED, "emit": _lib.GRID_PAIRS_EMIT,
+                "per_object": _lib.GRID_PAIRS_PER_OBJECT}
+
+    def __init__(self, device: int = 0, radix_bits: int = 0, pair_gen: str = "fused"):
         import torch
         self._torch = torch
         self.device = torch.device("cuda", device)
         self._lib = _lib.load()
         opts = GridOpts()
         opts.radix_bits = int(radix_bits)
+        opts.pair_gen = self.PAIR_GEN[pair_gen]
         h = ctypes.c_void_p()
         check(self._lib.grid_ctx_create(int(device), ctypes.byref(opts), ctypes.byref(h)), "grid_ctx_create")
         self._h = h
@@ -255,6 +259,19 @@ class Context:
         ci = info.to_c()
         check(self._lib.grid_emit_pairs(self._h, recs.data_ptr(), recs.shape[0], int(nrefs), ctypes.byref(ci),
                                         C.data_ptr(), O.data_ptr()), "grid_emit_pairs")
+        return C, O
+
+    def emit_pairs_per_object(self, recs, nrefs: int, info: Info):
+        """The same object-order (C, O), one thread per object (the sorted
+        grid's MakePairs; an ablation)."""
+        torch = self._torch
+        C = torch.empty(nrefs, dtype=torch.int32, device=self.device)
+        O = torch.empty(nrefs, dtype=torch.int32, device=self.device)
+        self._bind_stream()
+        ci = info.to_c()
+        check(self._lib.grid_emit_pairs_per_object(self._h, recs.data_ptr(), recs.shape[0], int(nrefs),
+                                                   ctypes.byref(ci), C.data_ptr(), O.data_ptr()),
+              "grid_emit_pairs_per_object")
         return C, O
 
     def sort_pairs(self, C, O, key_bits: int):

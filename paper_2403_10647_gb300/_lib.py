@@ -19,6 +19,9 @@ GRID_ENOSPC = -7
 GRID_ENOTREADY = -8
 GRID_ELIMIT = -9
 GRID_RES_MAX = 65535
+GRID_PAIRS_FUSED = 0
+GRID_PAIRS_EMIT = 1
+GRID_PAIRS_PER_OBJECT = 2
 
 c_int32, c_int64, c_float, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
 P = ctypes.POINTER
@@ -52,7 +55,7 @@ class GridKernelStat(ctypes.Structure):
 
 
 class GridOpts(ctypes.Structure):
-    _fields_ = [("radix_bits", c_int32), ("reserved", c_int32 * 7)]
+    _fields_ = [("radix_bits", c_int32), ("pair_gen", c_int32), ("reserved", c_int32 * 6)]
 
 
 class GridServeOpts(ctypes.Structure):
@@ -91,6 +94,8 @@ SIGNATURES = {
     "grid_count_scan": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, P(GridInfo), c_void_p,
                                   P(c_int64)]),
     "grid_emit_pairs": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, P(GridInfo), c_void_p, c_void_p]),
+    "grid_emit_pairs_per_object": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, P(GridInfo), c_void_p,
+                                             c_void_p]),
     "grid_sort_pairs": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p]),
     "grid_extract_ranges": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "grid_extract_ranges_noalloc": (c_int32, [c_void_p, c_int64, c_int64, c_void_p, c_void_p]),

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(REPO_DIR, "include")
 BUILD_DIR = os.path.join(PKG_DIR, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libgrid.so")
 
-SOURCES = ["kernels.cu", "runtime.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["kernels.cu", "runtime.cu", "noalloc.cu", "serve.cu", "sorted_grid.cu"]
 HEADERS = ["device.cuh", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -162,6 +162,10 @@ cudaError_t launch_count_scan(const CountArgs &a, cudaStream_t s);
 cudaError_t launch_tile_search(const ObjRec *recs, long long n, unsigned tile, unsigned ntiles,
                                unsigned *tile_obj, cudaStream_t s);
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s);
+// Pair-generation ablation (sorted_grid.cu): one thread per object writes its
+// pairs C[start ..], O[start ..] (single mesh).
+cudaError_t launch_make_pairs_per_object(const ObjRec *recs, long long n, unsigned res_x, unsigned res_y,
+                                         unsigned count, unsigned *C, unsigned *O, Ctl *ctl, cudaStream_t s);
 cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s);
 cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, int nsm, cudaStream_t s);
 unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells);

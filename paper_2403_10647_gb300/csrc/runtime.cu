@@ -44,11 +44,12 @@ struct Scratch {
 };
 
 enum KernelId {
-    K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_LOCALIZE, K_NUM
+    K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_LOCALIZE,
+    K_PER_OBJECT, K_NUM
 };
 const char *const kKernelNames[K_NUM] = {"bounds",  "count_scan",    "tile_search",   "emit",
                                          "upsweep_gen", "downsweep_gen", "upsweep", "downsweep",
-                                         "extract_split", "extract",   "localize"};
+                                         "extract_split", "extract",   "localize", "make_pairs_per_object"};
 
 struct PendingTiming {
     int kid;
@@ -65,6 +66,7 @@ struct grid_ctx {
     cudaMemPool_t pool = nullptr;
     grid_opts opts{};
     int rbits_max = 9;
+    int pair_gen = GRID_PAIRS_FUSED;
 
     Ctl *d_ctl = nullptr;        // device control block
     Ctl *h_ctl = nullptr;        // pinned host mirror
@@ -74,6 +76,7 @@ struct grid_ctx {
     Scratch recs, k2status, tile_obj, keys_sorted, keys[1], vals[1], intra, gpref, gstatus, splits;
     Scratch in_verts, in_tris, out_cells, out_refs;  // host-buffer builds
     Scratch b_desc, b_base, b_state, b_pairbase, b_cellsoff, b_G;   // batched builds
+    Scratch pairs_C, pairs_O;    // object-order pairs of the unfused pair_gen modes
     std::atomic<int64_t> in_use{0};
 
     // per-kernel accounting
@@ -486,17 +489,35 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
         }
         GG_TRY(ensure(c, c->keys_sorted, (size_t)count * sizeof(unsigned)));
         unsigned *keys_sorted = (unsigned *)c->keys_sorted.ptr;
-        if (sc.passes == 0) {
-            gg::EmitArgs ea{};
-            ea.recs = recs;
-            ea.tile_obj = tile_obj;
-            ea.res_x = (unsigned)I.res[0];
-            ea.res_y = (unsigned)I.res[1];
-            ea.count = count;
-            ea.C = keys_sorted;
-            ea.O = refs;
-            KernelScope ks(c, K_EMIT, 16.0 * n + 8.0 * count);
-            GG_CUDA(gg::launch_emit(ea, c->stream));
+        if (sc.passes == 0 || c->pair_gen != GRID_PAIRS_FUSED) {
+            // object-order (C, O) in device memory: straight into the outputs
+            // when there is nothing to sort, else into scratch for the sort
+            unsigned *C = keys_sorted, *O = refs;
+            if (sc.passes > 0) {
+                GG_TRY(ensure(c, c->pairs_C, (size_t)count * sizeof(unsigned)));
+                GG_TRY(ensure(c, c->pairs_O, (size_t)count * sizeof(unsigned)));
+                C = (unsigned *)c->pairs_C.ptr;
+                O = (unsigned *)c->pairs_O.ptr;
+            }
+            if (c->pair_gen == GRID_PAIRS_PER_OBJECT) {
+                KernelScope ks(c, K_PER_OBJECT, 16.0 * n + 8.0 * count);
+                GG_CUDA(gg::launch_make_pairs_per_object(recs, n, (unsigned)I.res[0], (unsigned)I.res[1], count, C,
+                                                         O, c->d_ctl, c->stream));
+            } else {
+                gg::EmitArgs ea{};
+                ea.recs = recs;
+                ea.tile_obj = tile_obj;
+                ea.res_x = (unsigned)I.res[0];
+                ea.res_y = (unsigned)I.res[1];
+                ea.count = count;
+                ea.C = C;
+                ea.O = O;
+                KernelScope ks(c, K_EMIT, 16.0 * n + 8.0 * count);
+                GG_CUDA(gg::launch_emit(ea, c->stream));
+            }
+            if (sc.passes > 0)
+                GG_TRY(sort_pairs(c, sc, count, false, nullptr, 0, nullptr, 0, 0, gg::MeshTab{}, C, O, keys_sorted,
+                                  refs));
         } else {
             GG_TRY(sort_pairs(c, sc, count, true, recs, n, tile_obj, (unsigned)I.res[0], (unsigned)I.res[1],
                               gg::MeshTab{}, nullptr, nullptr, keys_sorted, refs));
@@ -591,6 +612,11 @@ int grid_ctx_create(int device, const grid_opts *opts, grid_ctx **out)
     c->device = device;
     if (opts) c->opts = *opts;
     if (c->opts.radix_bits >= 8 && c->opts.radix_bits <= 11) c->rbits_max = c->opts.radix_bits;
+    if (c->opts.pair_gen < GRID_PAIRS_FUSED || c->opts.pair_gen > GRID_PAIRS_PER_OBJECT) {
+        delete c;
+        return GRID_EINVAL;
+    }
+    c->pair_gen = c->opts.pair_gen;
     int rc = GRID_OK;
     do {
         if ((rc = cuda_err(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device)))) break;
@@ -631,7 +657,7 @@ void grid_ctx_destroy(grid_ctx *c)
         Scratch *all[] = {&c->recs, &c->k2status, &c->tile_obj, &c->splits, &c->keys_sorted, &c->keys[0],
                           &c->vals[0], &c->intra, &c->gpref, &c->gstatus, &c->in_verts, &c->in_tris,
                           &c->out_cells, &c->out_refs, &c->b_desc, &c->b_base, &c->b_state, &c->b_pairbase,
-                          &c->b_cellsoff, &c->b_G};
+                          &c->b_cellsoff, &c->b_G, &c->pairs_C, &c->pairs_O};
         for (Scratch *s : all) release(c, *s);
         if (c->stream) cudaStreamSynchronize(c->stream);
         resolve_timings(c);
@@ -1029,6 +1055,24 @@ int grid_emit_pairs(grid_ctx *c, const grid_objrec *recs, int64_t n, int64_t nre
     {
         KernelScope ks(c, K_EMIT, 16.0 * n + 8.0 * nrefs);
         GG_CUDA(gg::launch_emit(ea, c->stream));
+    }
+    GG_TRY(read_ctl(c));
+    return ctl_error(c->h_ctl->err);
+}
+
+int grid_emit_pairs_per_object(grid_ctx *c, const grid_objrec *recs, int64_t n, int64_t nrefs,
+                               const grid_info *info, int32_t *C, int32_t *O)
+{
+    if (!c || !info || n < 0 || nrefs < 0 || nrefs > kInt32Max) return GRID_EINVAL;
+    if (nrefs == 0) return GRID_OK;
+    if (n == 0 || !recs || !C || !O) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    GG_TRY(reset_ctl(c));
+    {
+        KernelScope ks(c, K_PER_OBJECT, 16.0 * n + 8.0 * nrefs);
+        GG_CUDA(gg::launch_make_pairs_per_object((const ObjRec *)recs, n, (unsigned)info->res[0],
+                                                 (unsigned)info->res[1], (unsigned)nrefs, (unsigned *)C,
+                                                 (unsigned *)O, c->d_ctl, c->stream));
     }
     GG_TRY(read_ctl(c));
     return ctl_error(c->h_ctl->err);

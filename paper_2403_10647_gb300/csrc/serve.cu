@@ -11,8 +11,9 @@
 //     request (in arrival order, up to max_batch and batch_pairs estimated
 //     pairs) and builds them as one flattened problem with
 //     grid_build_batched, so many small rebuilds share one launch per step;
-//   * jitter on the device: one launch per batch writes each request's
-//     perturbed vertices into the worker's vertex buffer;
+//   * jitter on the device (jitter_kernel below, also behind grid_jitter):
+//     one launch per batch writes each request's perturbed vertices into the
+//     worker's vertex buffer;
 //   * admission by device memory: each admitted request reserves an estimate
 //     of its bytes until its result is released; submissions beyond the
 //     budget are refused (GRID_EAGAIN) rather than queued without bound;
@@ -101,6 +102,79 @@ double percentile(std::vector<double> v, double q)
 }
 
 }  // namespace
+
+namespace gg {
+
+// ---------------------------------------------------------------------------
+// per-request vertex jitter (serving loop)
+// ---------------------------------------------------------------------------
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the
+// round constants 0xD2511F53 / 0xCD9E8D57, the key bumped by the Weyl
+// increments 0x9E3779B9 / 0xBB67AE85 after every round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Unit-variance normal as an Irwin-Hall sum of four 24-bit uniforms, minus
+// its mean 2 (variance 4/12, so the caller's factor is sigma * sqrt(3)).
+// Every step is one float add in round-to-nearest: the host generator of the
+// tests performs the same operations in the same order.
+__device__ __forceinline__ float irwin_hall4(uint4 x)
+{
+    const float q = 5.9604644775390625e-8f;   // 2^-24
+    const float u0 = __fmul_rn(__uint2float_rn(x.x >> 8), q);
+    const float u1 = __fmul_rn(__uint2float_rn(x.y >> 8), q);
+    const float u2 = __fmul_rn(__uint2float_rn(x.z >> 8), q);
+    const float u3 = __fmul_rn(__uint2float_rn(x.w >> 8), q);
+    return __fsub_rn(__fadd_rn(__fadd_rn(u0, u1), __fadd_rn(u2, u3)), 2.0f);
+}
+
+__global__ void __launch_bounds__(256) jitter_kernel(JitterDesc one, const JitterDesc *__restrict__ d,
+                                                     const long long *__restrict__ ebase, int nm, long long total)
+{
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < total; e += (long long)gridDim.x * 256) {
+        JitterDesc jd = one;
+        long long local = e;
+        if (d) {   // owner: the last mesh whose first element is <= e
+            int lo = 0, hi = nm - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ebase[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            jd = d[lo];
+            local = e - ebase[lo];
+        }
+        const unsigned long long i = (unsigned long long)local / 3ull;
+        const unsigned a = (unsigned)(local - 3ll * (long long)i);
+        const uint4 x = philox4x32_10(make_uint4((unsigned)i, a, 0u, 0u), (unsigned)jd.seed,
+                                      (unsigned)(jd.seed >> 32));
+        jd.dst[local] = __fadd_rn(jd.src[local], __fmul_rn(irwin_hall4(x), jd.s));
+    }
+}
+
+cudaError_t launch_jitter(const JitterDesc &one, const JitterDesc *d, const long long *ebase, int nm,
+                          long long total, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    const long long want = (total + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 4864 ? want : 4864);   // 152 SMs x 32 blocks, grid-stride beyond
+    jitter_kernel<<<blocks, 256, 0, s>>>(one, d, ebase, nm, total);
+    return cudaGetLastError();
+}
+
+}  // namespace gg
 
 struct grid_server {
     int device = 0;

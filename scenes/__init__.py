@@ -152,6 +152,17 @@ def architectural(n: int = 10_000_000, seed: int = SEED_BASE + 3, lam: float = 8
     return Scene(f"architectural_{n}", verts, tris, lam)
 
 
+def architectural_scaled(n: int, seed: int = SEED_BASE + 3, lam: float = 8.0) -> Scene:
+    """The architectural scene with n triangles at the 10M scene's density:
+    building 200 x 50 x 200 scaled by cbrt(n / 1e7), 2000 * n / 1e7 clutter
+    blobs (at least 4)."""
+    f = (n / 1e7) ** (1.0 / 3.0)
+    s = architectural(n, seed=seed, lam=lam, size=(200.0 * f, 50.0 * f, 200.0 * f),
+                      nblobs=max(4, int(round(2000 * n / 1e7))))
+    s.name = f"architectural_scaled_{n}"
+    return s
+
+
 def batch_sizes(nmeshes: int = 64, seed: int = SEED_BASE + 4, lo: float = 1e3, hi: float = 2e6):
     """Triangle counts log-uniform in [lo, hi] for a batch of meshes."""
     g = rng(seed)
@@ -186,9 +197,7 @@ def serving_pool(nmeshes: int = 12, seed: int = SEED_BASE + 5, lo: float = 1e4, 
     for k, (nk, is_arch) in enumerate(zip(sizes, arch)):
         nk = int(nk)
         if is_arch:
-            f = (nk / 1e7) ** (1.0 / 3.0)
-            out.append(architectural(nk, seed=seed * 1000 + k, size=(200.0 * f, 50.0 * f, 200.0 * f),
-                                     nblobs=max(4, int(round(2000 * nk / 1e7)))))
+            out.append(architectural_scaled(nk, seed=seed * 1000 + k))
         else:
             out.append(nonhomogeneous_soup(nk, seed=seed * 1000 + k, extent=100.0 * (nk / 1e6) ** (1.0 / 3.0)))
     return out

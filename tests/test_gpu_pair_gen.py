@@ -1,0 +1,100 @@
+"""The pair-generation modes of grid_build (grid_opts.pair_gen) against the
+oracle: the paper's unfused chain (pairs written to device memory, then
+sorted) and the sorted grid's one-thread-per-object MakePairs (an ablation)
+must give the same object-order pairs and the same grid as the default fused
+path, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+MODES = ["emit", "per_object"]
+
+
+def dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def mode_ctx():
+    import paper_2403_10647_gb300 as pg
+    ctxs = {m: pg.Context(0, pair_gen=m) for m in MODES}
+    yield ctxs
+    for c in ctxs.values():
+        c.close()
+
+
+SCENES = [
+    ("uniform_20k", lambda: scenes.uniform_soup(20_000, seed=401)),
+    ("nonhomog_30k", lambda: scenes.nonhomogeneous_soup(30_000, seed=402, extent=30.0)),
+    ("arch_60k", lambda: scenes.architectural(60_000, seed=403, size=(40.0, 10.0, 40.0), nblobs=40)),
+    ("one_triangle", lambda: scenes.Scene("one", np.array([[0, 0, 0], [1, 0.5, 0.2], [0.3, 1, 0.9]], np.float32),
+                                          np.array([[0, 1, 2]], np.int32), 64.0)),
+    ("empty", lambda: scenes.Scene("empty", np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), 2.0)),
+]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name,make", SCENES, ids=[n for n, _ in SCENES])
+def test_modes_match_oracle(ctx, mode_ctx, mode, name, make):
+    s = make()
+    g = mode_ctx[mode].build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+    o = oracle.build_grid(s.verts, s.tris, s.lam)
+    assert tuple(g.info.res) == tuple(o.plan.res) and g.info.nrefs == o.NO
+    assert np.array_equal(host(g.cells), o.G), (mode, name)
+    assert np.array_equal(host(g.refs), o.refs), (mode, name)
+    if s.n:
+        f = ctx.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+        assert torch.equal(f.cells, g.cells) and torch.equal(f.refs, g.refs)
+
+
+def test_per_object_pairs_match_oracle(ctx):
+    """grid_emit_pairs_per_object writes the object-order lists of Algorithm 1
+    (MakeObjectIds .. MakeCellIds), as grid_emit_pairs does."""
+    import paper_2403_10647_gb300 as pg
+    s = scenes.nonhomogeneous_soup(40_000, seed=404, extent=35.0)
+    v, t = dev(s.verts, torch.float32), dev(s.tris, torch.int32)
+    lo, hi = ctx.bounds(v, t)
+    info = pg.plan(lo, hi, s.n, s.lam)
+    recs, nrefs = ctx.count_scan(v, t, info)
+    info.nrefs = nrefs
+    C, O = ctx.emit_pairs_per_object(recs, nrefs, info)
+    p = oracle.plan(*oracle.bounds(s.verts, s.tris), s.n, s.lam)
+    clo, chi, V = oracle.cell_boxes(s.verts, s.tris, p)
+    off, NO = oracle.exclusive_sum(V)
+    oC, oO = oracle.object_order_pairs(clo, chi, off, NO, p.res)
+    assert nrefs == NO
+    assert np.array_equal(host(C), oC) and np.array_equal(host(O), oO)
+    C2, O2 = ctx.emit_pairs(recs, nrefs, info)
+    assert torch.equal(C, C2) and torch.equal(O, O2)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", MODES)
+def test_modes_full_size_nonhomogeneous(ctx, mode_ctx, mode):
+    """The 1M-triangle non-homogeneous scene (single triangles covering up to
+    ~1e5 cells) in every mode equals the default build."""
+    s = scenes.CONFIGS["nonhomogeneous_1e6"]()
+    v, t = dev(s.verts, torch.float32), dev(s.tris, torch.int32)
+    f = ctx.build(v, t, s.lam)
+    g = mode_ctx[mode].build(v, t, s.lam)
+    assert torch.equal(f.cells, g.cells) and torch.equal(f.refs, g.refs)
+
+
+def test_bad_mode_rejected():
+    import ctypes
+    from paper_2403_10647_gb300 import _lib
+    lib = _lib.load()
+    o = _lib.GridOpts()
+    o.pair_gen = 7
+    h = ctypes.c_void_p()
+    assert lib.grid_ctx_create(0, ctypes.byref(o), ctypes.byref(h)) == _lib.GRID_EINVAL
