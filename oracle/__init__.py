@@ -17,7 +17,10 @@ Entry points (numpy in, numpy out):
 * ``ranges`` - RunLengthEncode, NonEmptyCells, ExclusiveSum -> G;
 * ``build_grid`` - the whole chain, either literally (``method="alg1"``) or by the
   counting placement (``method="counting"``, O(NO), for large scenes);
-* ``grid_bruteforce`` - every (cell, object) pair tested directly (tiny only).
+* ``grid_bruteforce`` - every (cell, object) pair tested directly (tiny only);
+* ``tri_cell_separated`` / ``cull_pairs`` / ``place_stable`` and
+  ``build_grid(..., cull=True)`` - the false-intersection culling mode (a
+  triangle/cell separating-axis test before the sort, Sec. 6's future work).
 """
 from __future__ import annotations
 
@@ -78,6 +81,9 @@ def _bind(lib):
         "or_ranges": [P, I64, I64, P],
         "or_grid_counting": [P, P, I64, P, I64, P, P],
         "or_grid_bruteforce": [P, P, I64, P, P, P, I64, P],
+        "or_tri_cell_separated": [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+        "or_cull_pairs": [P, P, I64, P, P, P, P, P, I64, P, P, P, P],
+        "or_place_stable": [P, P, I64, I64, P, P],
     }.items():
         fn = getattr(lib, name)
         fn.argtypes = args
@@ -231,6 +237,53 @@ def grid_bruteforce(clo, chi, p: Plan, cap: int | None = None):
     return G, refs[: int(nr[0])].copy()
 
 
+def tri_cell_separated(q, x: int, y: int, z: int) -> bool:
+    """The culling test: is the triangle with grid-space vertices q
+    (float32[3, 3], row = vertex) separated from cell (x, y, z)?"""
+    lib = _load()
+    q = _c(q, np.float32, (9,))
+    return bool(lib.or_tri_cell_separated(_p(q), int(x), int(y), int(z)))
+
+
+def grid_space(verts, tris, p: Plan):
+    """q float32[n, 3, 3]: each triangle's vertices in grid coordinates,
+    (v - lo) * scale with both operations rounded to FP32 (numpy float32
+    arithmetic: one rounding per operation)."""
+    v = _c(verts, np.float32, (-1, 3))
+    t = _c(tris, np.int32, (-1, 3))
+    return ((v[t] - p.lo[None, None, :]).astype(np.float32) * p.scale[None, None, :]).astype(np.float32)
+
+
+def cull_pairs(verts, tris, p: Plan, clo, chi, cap: int):
+    """Box-placement pairs minus the culled ones, in object order:
+    (C int32[NOk], O int32[NOk], kept int64[n])."""
+    lib = _load()
+    v = _c(verts, np.float32, (-1, 3))
+    t = _c(tris, np.int32, (-1, 3))
+    clo = _c(clo, np.int32, (-1, 3))
+    chi = _c(chi, np.int32, (-1, 3))
+    n = t.shape[0]
+    C = np.zeros(max(cap, 1), np.int32)
+    O = np.zeros(max(cap, 1), np.int32)
+    kept = np.zeros(n, np.int64)
+    nk = np.zeros(1, np.int64)
+    _check(lib.or_cull_pairs(_p(v), _p(t), n, _p(p.lo), _p(p.scale), _p(p.res), _p(clo), _p(chi), cap,
+                             _p(C), _p(O), _p(kept), _p(nk)), "cull_pairs")
+    k = int(nk[0])
+    return C[:k].copy(), O[:k].copy(), kept
+
+
+def place_stable(C, O, ncells: int):
+    """Stable counting placement of object-order pairs -> (G, refs)."""
+    lib = _load()
+    C = _c(C, np.int32)
+    O = _c(O, np.int32)
+    G = np.zeros(ncells + 1, np.int32)
+    refs = np.zeros(max(C.shape[0], 1), np.int32)
+    _check(lib.or_place_stable(_p(C), _p(O), C.shape[0], ncells, _p(G), _p(refs)), "place_stable")
+    return G, refs[: C.shape[0]].copy()
+
+
 @dataclasses.dataclass
 class Grid:
     plan: Plan
@@ -243,13 +296,26 @@ class Grid:
     offsets: np.ndarray | None = None
 
 
-def build_grid(verts, tris, lam: float, method: str = "alg1") -> Grid:
-    """BuildParallelGrid: boxes -> M -> ... -> (G, O)."""
+def build_grid(verts, tris, lam: float, method: str = "alg1", cull: bool = False) -> Grid:
+    """BuildParallelGrid: boxes -> M -> ... -> (G, O).  With cull, the pairs a
+    triangle/cell separating-axis test rejects are removed before the sort
+    (the culling mode; NO is then the kept count and V the kept counts per
+    object): "alg1" sorts the kept lists with the stable sort + range steps,
+    any other method uses the stable counting placement."""
     lo, hi = bounds(verts, tris)
     n = int(np.asarray(tris).reshape(-1, 3).shape[0])
     p = plan(lo, hi, n, lam)
     clo, chi, V = cell_boxes(verts, tris, p)
     off, NO = exclusive_sum(V)
+    if cull:
+        C, O, kept = cull_pairs(verts, tris, p, clo, chi, NO)
+        if method == "alg1":
+            Cs, Os = sort_pairs(C, O)
+            G, refs = ranges(Cs, p.ncells), Os
+        else:
+            G, refs = place_stable(C, O, p.ncells)
+        koff, NOk = exclusive_sum(kept)
+        return Grid(p, G, refs, NOk, clo, chi, kept, koff)
     if method == "alg1":
         C, O = object_order_pairs(clo, chi, off, NO, p.res)
         Cs, Os = sort_pairs(C, O)

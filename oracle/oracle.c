@@ -340,3 +340,153 @@ int or_grid_bruteforce(const int32_t *clo, const int32_t *chi, int64_t n, const 
     *nrefs = k;
     return OR_OK;
 }
+
+/* ---- False-intersection culling (Sec. 6, future work) ----------------------
+ *
+ * The box placement above lists an object in every cell of its bounding box,
+ * so a long diagonal triangle lands in many cells it does not touch.  The
+ * paper names a triangle/cell overlap test ahead of the sort as future work.
+ * This is that test, with one fixed reading:
+ *
+ *   grid-space vertex  q_k = (v_k - lo) * scale per axis: the two FP32
+ *                      operations of the cell mapping, so floor(q) is the
+ *                      vertex's cell;
+ *   cell (x, y, z)     the closed unit cube centred at c = (x, y, z) + 1/2;
+ *   local vertex       w_k = q_k - c;
+ *   edges              e_0 = q_1 - q_0, e_1 = q_2 - q_1, e_2 = q_0 - q_2;
+ *   axes               the normal n = e_0 x e_1 and, for each edge e and unit
+ *                      axis, unit x e: (0, -e_z, e_y), (e_z, 0, -e_x) and
+ *                      (-e_y, e_x, 0) (separating-axis theorem for a
+ *                      triangle against a box);
+ *   projection         p_k = (a_x w_kx + a_y w_ky) + a_z w_kz;
+ *   box radius         S = (|a_x| + |a_y|) + |a_z|, r = S / 2;
+ *   slack              t = W 2^-16 + 2^-10 with W = max_{k,a} |w_ka|, and
+ *                      R = r + S t;
+ *   separated          min_k p_k > R or max_k p_k < -R.
+ *
+ * A pair is dropped iff one of the ten axes separates.  Every product, sum and
+ * difference is a single FP32 operation in the order written (no fused
+ * multiply-add), so the decision is exact and machine-independent.  The
+ * rounding error of p_k is a few units of 2^-24 S W, far below the slack
+ * S t, so a triangle that touches the closed cell is never dropped, while a
+ * cell that an axis separates by more than about t cell widths always is.
+ * The three face normals are not tested: each cell of the object's cell box
+ * already meets the triangle's extent along x, y and z.
+ *
+ * Both triangle and cell are the grid-space ones; the world-space triangle
+ * differs from the grid-space one by the rounding of the cell mapping only. */
+
+#define OR_SLACK_REL 0x1p-16f
+#define OR_SLACK_ABS 0x1p-10f
+
+/* 1 if the triangle with grid-space vertices q (q[3k + a]) is separated from
+ * cell (x, y, z), else 0. */
+int or_tri_cell_separated(const float *q, int32_t x, int32_t y, int32_t z)
+{
+    const float c[3] = {(float)x + 0.5f, (float)y + 0.5f, (float)z + 0.5f};
+    float w[3][3];
+    float W = 0.0f;
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a) {
+            w[k][a] = q[3 * k + a] - c[a];
+            W = fmaxf(W, fabsf(w[k][a]));
+        }
+    const float t = W * OR_SLACK_REL + OR_SLACK_ABS;
+    float e[3][3];
+    for (int a = 0; a < 3; ++a) {
+        e[0][a] = q[3 + a] - q[a];
+        e[1][a] = q[6 + a] - q[3 + a];
+        e[2][a] = q[a] - q[6 + a];
+    }
+    float ax[10][3];
+    ax[0][0] = e[0][1] * e[1][2] - e[0][2] * e[1][1];
+    ax[0][1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];
+    ax[0][2] = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+    for (int j = 0; j < 3; ++j) {
+        ax[1 + j][0] = 0.0f;
+        ax[1 + j][1] = -e[j][2];
+        ax[1 + j][2] = e[j][1];
+        ax[4 + j][0] = e[j][2];
+        ax[4 + j][1] = 0.0f;
+        ax[4 + j][2] = -e[j][0];
+        ax[7 + j][0] = -e[j][1];
+        ax[7 + j][1] = e[j][0];
+        ax[7 + j][2] = 0.0f;
+    }
+    for (int s = 0; s < 10; ++s) {
+        const float *a = ax[s];
+        float pmin = 0.0f, pmax = 0.0f;
+        for (int k = 0; k < 3; ++k) {
+            float p = a[0] * w[k][0] + a[1] * w[k][1];
+            p = p + a[2] * w[k][2];
+            if (k == 0 || p < pmin) pmin = p;
+            if (k == 0 || p > pmax) pmax = p;
+        }
+        const float S = (fabsf(a[0]) + fabsf(a[1])) + fabsf(a[2]);
+        const float R = 0.5f * S + S * t;
+        if (pmin > R || pmax < -R) return 1;
+    }
+    return 0;
+}
+
+/* The object-order pair lists of the box placement with the separated pairs
+ * removed: objects ascending, each object's box cells in GlobalCoords order
+ * (x fastest), a cell kept iff or_tri_cell_separated says 0.  kept[i] gets
+ * object i's kept count.  C, O hold cap entries; *NOk gets the number kept
+ * (OR_EOVERFLOW if it would pass cap or INT32_MAX).  Inputs must have passed
+ * or_bounds, and clo / chi come from or_cell_boxes on the same plan. */
+int or_cull_pairs(const float *verts, const int32_t *tris, int64_t n, const float lo[3],
+                  const float scale[3], const int32_t res[3], const int32_t *clo, const int32_t *chi,
+                  int64_t cap, int32_t *C, int32_t *O, int64_t *kept, int64_t *NOk)
+{
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        float q[9];
+        for (int v = 0; v < 3; ++v)
+            for (int a = 0; a < 3; ++a) {
+                float t = verts[3 * (int64_t)tris[3 * i + v] + a] - lo[a];
+                q[3 * v + a] = t * scale[a];
+            }
+        const int32_t *l = &clo[3 * i], *h = &chi[3 * i];
+        int64_t ki = 0;
+        for (int32_t z = l[2]; z <= h[2]; ++z)
+            for (int32_t y = l[1]; y <= h[1]; ++y)
+                for (int32_t x = l[0]; x <= h[0]; ++x) {
+                    if (or_tri_cell_separated(q, x, y, z)) continue;
+                    if (k >= cap || k >= INT32_MAX) { *NOk = k; return OR_EOVERFLOW; }
+                    int32_t g3[3] = {x, y, z};
+                    C[k] = or_linear_cell(g3, res);
+                    O[k] = (int32_t)i;
+                    ++k;
+                    ++ki;
+                }
+        kept[i] = ki;
+    }
+    *NOk = k;
+    return OR_OK;
+}
+
+/* Stable counting placement of object-order pairs: G[c] = number of pairs
+ * with cell < c (G[ncells] = NO), refs = the objects in cell order, ties in
+ * input order.  A second, independent route to RadixSort + the range steps
+ * for pairs given as lists. */
+int or_place_stable(const int32_t *C, const int32_t *O, int64_t NO, int64_t ncells, int32_t *G,
+                    int32_t *refs)
+{
+    int64_t *cnt = (int64_t *)calloc((size_t)ncells + 1, sizeof(int64_t));
+    if (!cnt) return OR_ENOMEM;
+    for (int64_t j = 0; j < NO; ++j) {
+        if (C[j] < 0 || (int64_t)C[j] >= ncells) { free(cnt); return OR_EINVAL; }
+        cnt[C[j]] += 1;
+    }
+    int64_t s = 0;
+    for (int64_t c = 0; c <= ncells; ++c) {
+        int64_t v = cnt[c];
+        cnt[c] = s;
+        G[c] = (int32_t)s;
+        s += v;
+    }
+    for (int64_t j = 0; j < NO; ++j) refs[cnt[C[j]]++] = O[j];
+    free(cnt);
+    return OR_OK;
+}

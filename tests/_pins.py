@@ -20,7 +20,12 @@ What pins what:
     (scene bounds), cumsum (ExclusiveSum), stable argsort (RadixSort),
     searchsorted (G = number of sorted keys below each cell);
   * invariants: NO = sum V, segment lengths, every box cell emitted once,
-    G monotone with G[0] = 0 and G[ncells] = NO, ascending ids inside a cell.
+    G monotone with G[0] = 0 and G[ncells] = NO, ascending ids inside a cell;
+  * the culling mode: hand-worked cases (tests/golden/cull_example.txt), an
+    exact-rational separating-axis test cross-checked against exact polygon
+    clipping (the oracle never drops a touching cell and drops every clearly
+    separated one), and invariants on scenes (kept pairs are a subsequence of
+    the box pairs; vertex and interior-point cells are kept).
 """
 from __future__ import annotations
 
@@ -296,8 +301,169 @@ def pin_invariants():
         assert np.array_equal(cells_of_ref, C[perm])
 
 
+# ---- false-intersection culling ---------------------------------------------------
+
+def read_cull_cases() -> list:
+    cases, cur = [], None
+    with open(os.path.join(GOLDEN, "cull_example.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            key, *vals = line.split()
+            if key == "case":
+                cur = {"name": vals[0]}
+                cases.append(cur)
+            else:
+                cur[key] = [float(v) for v in vals]
+    return cases
+
+
+def pin_cull_hand():
+    """The hand-worked cases of tests/golden/cull_example.txt: each axis
+    family (the normal, u_x x e, u_y x e, u_z x e) separates exactly the
+    cells worked out by hand, and touching cells are kept."""
+    for case in read_cull_cases():
+        q = np.array(case["q"], np.float32).reshape(3, 3)
+        b = [int(v) for v in case["box"]]
+        kept = [(x, y, z) for z in range(b[2], b[5] + 1) for y in range(b[1], b[4] + 1)
+                for x in range(b[0], b[3] + 1) if not oracle.tri_cell_separated(q, x, y, z)]
+        want = [tuple(int(v) for v in case["kept"][i:i + 3]) for i in range(0, len(case["kept"]), 3)]
+        assert kept == want, (case["name"], kept, want)
+
+
+def _exact_clip_overlap(tri, cell):
+    """Exact (rational) test whether the closed triangle meets the closed
+    unit cube at integer corner `cell`: Sutherland-Hodgman clipping of the
+    triangle polygon by the cube's six half-spaces; non-empty means they
+    touch."""
+    from fractions import Fraction as F
+    poly = [tuple(F(c) for c in v) for v in tri]
+    for a in range(3):
+        for lo_side in (True, False):
+            bound = F(cell[a]) if lo_side else F(cell[a] + 1)
+
+            def d(pt):
+                return pt[a] - bound if lo_side else bound - pt[a]
+            out = []
+            for i in range(len(poly)):
+                P, Q = poly[i - 1], poly[i]
+                dp, dq = d(P), d(Q)
+                if dq >= 0:
+                    if dp < 0:
+                        t = dp / (dp - dq)
+                        out.append(tuple(P[k] + t * (Q[k] - P[k]) for k in range(3)))
+                    out.append(Q)
+                elif dp >= 0:
+                    t = dp / (dp - dq)
+                    out.append(tuple(P[k] + t * (Q[k] - P[k]) for k in range(3)))
+            poly = out
+            if not poly:
+                return False
+    return True
+
+
+def _exact_sat_gap(tri, cell):
+    """Exact separating-axis test over all 13 axes of a triangle and a box
+    (the three face normals, the triangle normal, the nine edge cross
+    products): the largest separation gap divided by the axis' L1 norm
+    (<= 0: the two touch or overlap)."""
+    from fractions import Fraction as F
+    v = [tuple(F(c) for c in p) for p in tri]
+    c = tuple(F(cell[a]) + F(1, 2) for a in range(3))
+    w = [tuple(p[a] - c[a] for a in range(3)) for p in v]
+    e = [tuple(v[(k + 1) % 3][a] - v[k][a] for a in range(3)) for k in range(3)]
+
+    def cross(a, b):
+        return (a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0])
+    units = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    axes = units + [cross(e[0], e[1])] + [cross(u, ek) for u in units for ek in e]
+    best = None
+    for ax in axes:
+        S = sum(abs(x) for x in ax)
+        if S == 0:
+            continue
+        p = [sum(ax[i] * wk[i] for i in range(3)) for wk in w]
+        gap = max(min(p) - S / 2, -S / 2 - max(p)) / S
+        best = gap if best is None else max(best, gap)
+    return best
+
+
+def pin_cull_exact(ntri: int = 150, seed: int = 15):
+    """Random triangles with dyadic grid coordinates (multiples of 1/32 in
+    [0, 6]) against every cell of their cell box, in exact rational
+    arithmetic: (1) the 13-axis separating-axis test and polygon clipping
+    agree on touch / no touch (pins the axis set); (2) the oracle never drops
+    a touching cell (conservative); (3) it drops every cell separated by more
+    than 2^-9 cell widths along an axis (tight, above the 2^-10 + W 2^-16
+    slack)."""
+    g = np.random.Generator(np.random.Philox(seed))
+    checked = dropped = 0
+    for _ in range(ntri):
+        base = g.integers(0, 4 * 32, 3)
+        spread = g.integers(1, 2 * 32, (3, 3)) * g.choice([-1, 1], (3, 3))
+        tri = np.clip(base[None, :] + spread * (g.random((3, 1)) < 0.8), 0, 6 * 32) / 32.0
+        if g.random() < 0.2:          # some flat in one axis, the grid planes included
+            tri[:, g.integers(0, 3)] = g.integers(0, 6 * 4) / 4.0
+        q = tri.astype(np.float32)
+        lo = np.floor(q.min(axis=0)).astype(int)
+        hi = np.floor(q.max(axis=0)).astype(int)
+        for z in range(lo[2], hi[2] + 1):
+            for y in range(lo[1], hi[1] + 1):
+                for x in range(lo[0], hi[0] + 1):
+                    touch = _exact_clip_overlap(q.tolist(), (x, y, z))
+                    gap = _exact_sat_gap(q.tolist(), (x, y, z))
+                    assert touch == (gap <= 0), (q.tolist(), (x, y, z), touch, gap)
+                    sep = oracle.tri_cell_separated(q, x, y, z)
+                    assert not (sep and touch), ("dropped a touching cell", q.tolist(), (x, y, z))
+                    if gap > 2.0 ** -9:
+                        assert sep, ("kept a separated cell", q.tolist(), (x, y, z), float(gap))
+                    checked += 1
+                    dropped += sep
+    assert checked > 1000 and dropped > 100, (checked, dropped)
+
+
+def pin_cull_invariants():
+    """On scenes: the kept pairs are a subsequence of the box pairs (object
+    order, GlobalCoords order inside an object); the cell of every vertex and
+    of sampled interior points of every triangle is kept; the two placements
+    of the kept pairs (stable sort + ranges, stable counting placement)
+    agree; large diagonal triangles lose most of their box cells."""
+    g = np.random.Generator(np.random.Philox(16))
+    for s in (scenes.uniform_soup(3000, seed=7), scenes.nonhomogeneous_soup(3000, seed=8, extent=15.0)):
+        full = oracle.build_grid(s.verts, s.tris, s.lam)
+        a = oracle.build_grid(s.verts, s.tris, s.lam, method="alg1", cull=True)
+        b = oracle.build_grid(s.verts, s.tris, s.lam, method="counting", cull=True)
+        assert np.array_equal(a.G, b.G) and np.array_equal(a.refs, b.refs) and a.NO == b.NO
+        assert a.G[0] == 0 and a.G[-1] == a.NO and (np.diff(a.G) >= 0).all()
+        p = a.plan
+        C, O = oracle.object_order_pairs(full.clo, full.chi, full.offsets, full.NO, p.res)
+        Ck, Ok, kept = oracle.cull_pairs(s.verts, s.tris, p, full.clo, full.chi, full.NO)
+        assert np.array_equal(kept, a.V) and kept.sum() == a.NO and (kept <= full.V).all()
+        key_full = O.astype(np.int64) * p.ncells + C
+        key_kept = Ok.astype(np.int64) * p.ncells + Ck
+        pos = np.searchsorted(key_full, key_kept)     # object-order keys are ascending
+        assert (np.diff(key_full) > 0).all() and np.array_equal(key_full[pos], key_kept)
+        kept_set = set(key_kept.tolist())
+        q = oracle.grid_space(s.verts, s.tris, p).astype(np.float64)
+        res = p.res.astype(np.int64)
+        bary = g.dirichlet((1, 1, 1), 12)
+        for i in range(s.n):
+            pts = np.concatenate([q[i], bary @ q[i]])
+            for pt in pts:
+                f = np.floor(pt)
+                if ((pt - f) < 1e-6).any() or ((f + 1 - pt) < 1e-6).any():
+                    continue      # on a cell face: either neighbour may hold it
+                cell = np.clip(f.astype(np.int64), 0, res - 1)
+                cid = int(cell[0] + res[0] * (cell[1] + res[1] * cell[2]))
+                assert i * p.ncells + cid in kept_set, (i, pt)
+        if "nonhomogeneous" in s.name:
+            assert a.NO < 0.5 * full.NO, (a.NO, full.NO)
+
+
 ALL_PINS = [pin_hand_example, pin_fig1_cells, pin_shifted_cells, pin_point_in_cell, pin_plan_cases, pin_plan_errors, pin_bounds,
-            pin_bruteforce, pin_brute_boxes, pin_library_routines, pin_invariants]
+            pin_bruteforce, pin_brute_boxes, pin_library_routines, pin_invariants,
+            pin_cull_hand, pin_cull_exact, pin_cull_invariants]
 
 
 def run_all():

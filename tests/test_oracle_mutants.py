@@ -38,8 +38,22 @@ MUTANTS = {
                          "int64_t v = g[c];\n        s += v;\n        G[c] = (int32_t)s;"),
     "cell_scale_dropped": ("float u = t * scale;", "float u = t;"),
     "cell_nan_not_zero": ("if (isnan(u)) return 0;\n    float f = floorf(u);", "float f = ceilf(u) - 1.0f;"),
-    "counting_exclusive_scan_shift": ("cnt[c] = s;\n        G[c] = (int32_t)s;",
-                                      "cnt[c] = s + v - v;\n        G[c] = (int32_t)(s + (c > 0));"),
+    "counting_exclusive_scan_shift": ("cnt[c] = s;\n        G[c] = (int32_t)s;\n        s += v;\n    }\n    for (int64_t i = 0;",
+                                      "cnt[c] = s + v - v;\n        G[c] = (int32_t)(s + (c > 0));\n        s += v;\n    }\n    for (int64_t i = 0;"),
+    # culling mode
+    "cull_normal_axis_dropped": ("for (int s = 0; s < 10; ++s) {", "for (int s = 1; s < 10; ++s) {"),
+    "cull_center_at_corner": ("(float)x + 0.5f, (float)y + 0.5f", "(float)x, (float)y + 0.5f"),
+    "cull_negative_slack": ("const float R = 0.5f * S + S * t;", "const float R = 0.5f * S - S * t;"),
+    "cull_radius_doubled": ("const float R = 0.5f * S + S * t;", "const float R = S + S * t;"),
+    "cull_edge_axis_sign": ("ax[1 + j][1] = -e[j][2];", "ax[1 + j][1] = e[j][2];"),
+    "cull_missing_edge": ("e[1][a] = q[6 + a] - q[3 + a];", "e[1][a] = q[6 + a] - q[a];"),
+    "cull_pmax_from_min": ("if (k == 0 || p > pmax) pmax = p;", "if (k == 0 || p < pmax) pmax = p;"),
+    "cull_last_vertex_skipped": ("for (int k = 0; k < 3; ++k) {\n            float p = a[0]",
+                                 "for (int k = 0; k < 2; ++k) {\n            float p = a[0]"),
+    "cull_normal_component_swapped": ("ax[0][1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];",
+                                      "ax[0][1] = e[0][0] * e[1][2] - e[0][2] * e[1][0];"),
+    "place_reversed": ("for (int64_t j = 0; j < NO; ++j) refs[cnt[C[j]]++] = O[j];",
+                       "for (int64_t j = NO - 1; j >= 0; --j) refs[cnt[C[j]]++] = O[j];"),
 }
 
 
