@@ -16,7 +16,11 @@ At one GPU the line also carries (unless --no-extras):
                           jitter: Poisson arrivals (--serve-rate per s for
                           --serve-seconds) with p50 / p99 latency, and a
                           saturated run against the same requests built back
-                          to back.
+                          to back;
+  pair_gen_ablation       fused pair generation vs the paper's unfused chain vs
+                          one thread per object (sorted-grid MakePairs);
+  culling                 the culled build (triangle/cell test before the sort)
+                          vs the box placement.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -288,6 +292,43 @@ def bench_pair_gen(scene, reps: int = 5):
     return out
 
 
+def bench_cull(scene, reps: int = 5):
+    """False-intersection culling: the culled build (grid_opts.cull) against
+    the box placement on the same scene; pair counts, ms per build (CUDA
+    events) and the culling kernel's own time."""
+    import torch
+    import paper_2403_10647_gb300 as pg
+    v = torch.from_numpy(scene.verts).cuda()
+    t = torch.from_numpy(scene.tris).cuda()
+    out = {"n_tris": scene.n}
+    for label, cull in (("box", False), ("culled", True)):
+        c = pg.Context(0, cull=cull)
+        try:
+            g = c.build(v, t, scene.lam)
+            out[f"{label}_nrefs"] = g.info.nrefs
+            del g
+            c.build(v, t, scene.lam)
+            c.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                g = c.build(v, t, scene.lam)
+                del g
+            e1.record()
+            torch.cuda.synchronize()
+            st = c.kernel_stats()
+            c.profile(False)
+            out[f"{label}_ms"] = e0.elapsed_time(e1) / reps
+            if cull:
+                out["cull_emit_ms"] = st["cull_emit"]["ms"] / reps
+        finally:
+            c.close()
+    out["kept_frac"] = out["culled_nrefs"] / max(out["box_nrefs"], 1)
+    out["speedup"] = out["box_ms"] / out["culled_ms"]
+    return out
+
+
 def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 4, max_batch: int = 32):
     """The rebuild-serving loop: a pool of registered meshes, requests with
     per-request jitter (sigma 0.01).  (1) open loop: Poisson arrivals at
@@ -503,8 +544,11 @@ def run_ours(args, rank, world, local):
         extras["batched_small"] = bench_batched(ctx, 0.01, reps=20)
         extras["serve"] = bench_serve(ctx, args.serve_seconds, args.serve_rate)
         extras["pair_gen_ablation"] = {args.workload: bench_pair_gen(scene)}
+        extras["culling"] = {args.workload: bench_cull(scene)}
         if args.workload != "nonhomogeneous_1e6":
-            extras["pair_gen_ablation"]["nonhomogeneous_1e6"] = bench_pair_gen(make_scene("nonhomogeneous_1e6"))
+            nh = make_scene("nonhomogeneous_1e6")
+            extras["pair_gen_ablation"]["nonhomogeneous_1e6"] = bench_pair_gen(nh)
+            extras["culling"]["nonhomogeneous_1e6"] = bench_cull(nh)
 
     in_mb = (scene.verts.nbytes + scene.tris.nbytes) / 1e6
     l2_note = (f"inputs larger than L2 ({in_mb:.0f} MB)" if in_mb > 129 else

@@ -103,7 +103,11 @@ typedef struct {
 typedef struct {
     int32_t radix_bits;   /* widest digit of the LSD radix sort: 8..11 (default 9) */
     int32_t pair_gen;     /* GRID_PAIRS_*; single-mesh builds only (batched builds always fuse) */
-    int32_t reserved[6];
+    int32_t cull;         /* 1: drop the pairs whose cell the triangle does not touch before the
+                             sort (grid_cull_pairs' test); single-mesh builds only.  The grid is
+                             then the culled grid: nrefs counts the kept pairs.  0: box placement
+                             (Algorithm 1 as published, the default) */
+    int32_t reserved[5];
 } grid_opts;
 
 /* ---- context -------------------------------------------------------------- */
@@ -226,6 +230,26 @@ int grid_emit_pairs(grid_ctx *ctx, const grid_objrec *recs, int64_t n, int64_t n
  * generation, not a step of Algorithm 1.  Same arguments and result. */
 int grid_emit_pairs_per_object(grid_ctx *ctx, const grid_objrec *recs, int64_t n, int64_t nrefs,
                                const grid_info *info, int32_t *C, int32_t *O);
+
+/* False-intersection culling (the overlap test ahead of the sort that Sec. 6
+ * names as future work; not a step of Algorithm 1): from the records of
+ * grid_count_scan, writes the object-order pairs of the box placement that a
+ * triangle/cell test keeps, compacted in the same order, into C and O (int32,
+ * capacity nrefs = the box placement's NO); *nkept gets their number
+ * (synchronises).  The test, in grid coordinates q = (v - lo) * scale (the
+ * cell mapping's two FP32 operations): cell (x, y, z) is the closed unit cube
+ * centred at c = (x, y, z) + 1/2; with w_k = q_k - c, edges e_0 = q_1 - q_0,
+ * e_1 = q_2 - q_1, e_2 = q_0 - q_2, axes n = e_0 x e_1 and (0, -e_z, e_y),
+ * (e_z, 0, -e_x), (-e_y, e_x, 0) for each edge, projections
+ * p_k = (a_x w_kx + a_y w_ky) + a_z w_kz, S = (|a_x| + |a_y|) + |a_z| and
+ * slack t = max|w| * 2^-16 + 2^-10, a cell is dropped iff for some axis
+ * min p > S/2 + S t or max p < -(S/2 + S t), each operation one FP32
+ * round-to-nearest step in that order.  The slack exceeds the rounding error,
+ * so a triangle touching the cell always keeps it.  GRID_EINVAL for a vertex
+ * index outside [0, nverts). */
+int grid_cull_pairs(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
+                    const grid_info *info, const grid_objrec *recs, int64_t nrefs, int32_t *C, int32_t *O,
+                    int64_t *nkept);
 
 /* a8, RadixSort(C, O) (Algorithm 1, Fig. 4c): stable LSD sort of the pairs by
  * the low key_bits bits of C (0..31; keys must be < 2^key_bits).  Writes

@@ -85,7 +85,7 @@ class Context:
     PAIR_GEN = {"fused": _lib.GRID_PAIRS_FUSED, "emit": _lib.GRID_PAIRS_EMIT,
                 "per_object": _lib.GRID_PAIRS_PER_OBJECT}
 
-    def __init__(self, device: int = 0, radix_bits: int = 0, pair_gen: str = "fused"):
+    def __init__(self, device: int = 0, radix_bits: int = 0, pair_gen: str = "fused", cull: bool = False):
         import torch
         self._torch = torch
         self.device = torch.device("cuda", device)
@@ -93,6 +93,7 @@ class Context:
         opts = GridOpts()
         opts.radix_bits = int(radix_bits)
         opts.pair_gen = self.PAIR_GEN[pair_gen]
+        opts.cull = 1 if cull else 0
         h = ctypes.c_void_p()
         check(self._lib.grid_ctx_create(int(device), ctypes.byref(opts), ctypes.byref(h)), "grid_ctx_create")
         self._h = h
@@ -260,6 +261,23 @@ class Context:
         check(self._lib.grid_emit_pairs(self._h, recs.data_ptr(), recs.shape[0], int(nrefs), ctypes.byref(ci),
                                         C.data_ptr(), O.data_ptr()), "grid_emit_pairs")
         return C, O
+
+    def cull_pairs(self, verts, tris, info: Info, recs, nrefs: int):
+        """False-intersection culling of the box pairs -> the kept (C, O) in
+        object order (int32 device tensors of the kept length)."""
+        torch = self._torch
+        v = self._dev(verts, torch.float32, 3)
+        t = self._dev(tris, torch.int32, 3)
+        C = torch.empty(max(nrefs, 1), dtype=torch.int32, device=self.device)
+        O = torch.empty(max(nrefs, 1), dtype=torch.int32, device=self.device)
+        self._bind_stream()
+        ci = info.to_c()
+        nk = ctypes.c_int64()
+        check(self._lib.grid_cull_pairs(self._h, v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], ctypes.byref(ci),
+                                        recs.data_ptr(), int(nrefs), C.data_ptr(), O.data_ptr(), ctypes.byref(nk)),
+              "grid_cull_pairs")
+        k = int(nk.value)
+        return C[:k], O[:k]
 
     def emit_pairs_per_object(self, recs, nrefs: int, info: Info):
         """The same object-order (C, O), one thread per object (the sorted

@@ -55,7 +55,7 @@ class GridKernelStat(ctypes.Structure):
 
 
 class GridOpts(ctypes.Structure):
-    _fields_ = [("radix_bits", c_int32), ("pair_gen", c_int32), ("reserved", c_int32 * 6)]
+    _fields_ = [("radix_bits", c_int32), ("pair_gen", c_int32), ("cull", c_int32), ("reserved", c_int32 * 5)]
 
 
 class GridServeOpts(ctypes.Structure):
@@ -94,6 +94,8 @@ SIGNATURES = {
     "grid_count_scan": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, P(GridInfo), c_void_p,
                                   P(c_int64)]),
     "grid_emit_pairs": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, P(GridInfo), c_void_p, c_void_p]),
+    "grid_cull_pairs": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, P(GridInfo), c_void_p, c_int64,
+                                  c_void_p, c_void_p, P(c_int64)]),
     "grid_emit_pairs_per_object": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, P(GridInfo), c_void_p,
                                              c_void_p]),
     "grid_sort_pairs": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p]),

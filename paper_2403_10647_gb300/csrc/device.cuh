@@ -29,8 +29,9 @@ struct Ctl {
     unsigned err;               // ERR_* bits
     unsigned hist_done;         // blocks of the digit-histogram kernel that finished
     unsigned long long nrefs;   // NO, written by the last count/scan tile
-    unsigned tickets[8];        // tile tickets: [0] count/scan, [1 + p] sort pass p
-    unsigned pad[6];
+    unsigned tickets[8];        // tile tickets: [0] count/scan, [7] culling emit
+    unsigned long long nkept;   // pairs the culling emit kept, written by its last tile
+    unsigned pad[4];
 };
 static_assert(sizeof(Ctl) == 96, "Ctl layout");
 

@@ -487,6 +487,195 @@ __global__ void __launch_bounds__(BLOCK) emit_kernel(EmitArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// False-intersection culling (the overlap test ahead of the sort that Sec. 6
+// leaves as future work): each box pair is tested, the kept ones are written
+// compacted, in object order.
+// ---------------------------------------------------------------------------
+
+// A triangle in grid space: vertices q (q[3k + a]), edges e_0 = q_1 - q_0,
+// e_1 = q_2 - q_1, e_2 = q_0 - q_2 and the normal n = e_0 x e_1.
+struct GridTri {
+    float q[9];
+    float e[9];
+    float n[3];
+};
+
+__device__ __forceinline__ void grid_tri(const float *__restrict__ verts, long long nverts,
+                                         const int *__restrict__ tris, unsigned o, const float (&lo)[3],
+                                         const float (&scale)[3], GridTri &t, Ctl *ctl)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int vi = __ldg(tris + 3ll * o + k);
+        if (vi < 0 || (long long)vi >= nverts) {   // never read outside verts: flag and use vertex 0
+            atomicOr(&ctl->err, ERR_BADINDEX);
+            vi = 0;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            t.q[3 * k + a] = __fmul_rn(__fsub_rn(__ldg(verts + 3ll * vi + a), lo[a]), scale[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        t.e[a] = __fsub_rn(t.q[3 + a], t.q[a]);
+        t.e[3 + a] = __fsub_rn(t.q[6 + a], t.q[3 + a]);
+        t.e[6 + a] = __fsub_rn(t.q[a], t.q[6 + a]);
+    }
+    t.n[0] = __fsub_rn(__fmul_rn(t.e[1], t.e[5]), __fmul_rn(t.e[2], t.e[4]));
+    t.n[1] = __fsub_rn(__fmul_rn(t.e[2], t.e[3]), __fmul_rn(t.e[0], t.e[5]));
+    t.n[2] = __fsub_rn(__fmul_rn(t.e[0], t.e[4]), __fmul_rn(t.e[1], t.e[3]));
+}
+
+// One separating axis a against the cell: projections of the local vertices
+// w, box radius S / 2 widened by the slack S t.  Each product and sum is one
+// round-to-nearest FP32 operation in a fixed order, so the decision is the
+// same on every IEEE machine.
+__device__ __forceinline__ bool axis_separates(float a0, float a1, float a2, const float (&w)[9], float t)
+{
+    float pmin = 0.0f, pmax = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float p = __fadd_rn(__fmul_rn(a0, w[3 * k]), __fmul_rn(a1, w[3 * k + 1]));
+        p = __fadd_rn(p, __fmul_rn(a2, w[3 * k + 2]));
+        pmin = k == 0 ? p : fminf(pmin, p);
+        pmax = k == 0 ? p : fmaxf(pmax, p);
+    }
+    const float S = __fadd_rn(__fadd_rn(fabsf(a0), fabsf(a1)), fabsf(a2));
+    const float R = __fadd_rn(__fmul_rn(0.5f, S), __fmul_rn(S, t));
+    return pmin > R || pmax < -R;
+}
+
+// The culling test: is triangle t separated from cell (x, y, z), the closed
+// unit cube centred at (x, y, z) + 1/2?  Axes: the normal, then unit x e for
+// every edge; slack t = max|w| 2^-16 + 2^-10 (bounds the rounding error of
+// the projections from above by a wide margin: a touching cell is never
+// rejected).
+__device__ __forceinline__ bool tri_cell_separated(const GridTri &t, unsigned x, unsigned y, unsigned z)
+{
+    const float c[3] = {__fadd_rn(__uint2float_rn(x), 0.5f), __fadd_rn(__uint2float_rn(y), 0.5f),
+                        __fadd_rn(__uint2float_rn(z), 0.5f)};
+    float w[9];
+    float W = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            w[3 * k + a] = __fsub_rn(t.q[3 * k + a], c[a]);
+            W = fmaxf(W, fabsf(w[3 * k + a]));
+        }
+    const float slack = __fadd_rn(__fmul_rn(W, 1.52587890625e-05f), 9.765625e-04f);   // 2^-16, 2^-10
+    if (axis_separates(t.n[0], t.n[1], t.n[2], w, slack)) return true;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float ex = t.e[3 * j], ey = t.e[3 * j + 1], ez = t.e[3 * j + 2];
+        if (axis_separates(0.0f, -ez, ey, w, slack)) return true;
+        if (axis_separates(ez, 0.0f, -ex, w, slack)) return true;
+        if (axis_separates(-ey, ex, 0.0f, w, slack)) return true;
+    }
+    return false;
+}
+
+template <int BLOCK, int ITEMS>
+__global__ void __launch_bounds__(BLOCK) cull_emit_kernel(CullArgs a)
+{
+    constexpr int T = BLOCK * ITEMS;
+    extern __shared__ __align__(16) unsigned smem[];
+    unsigned *s_mark = smem;                 // [padded T]: object marks, then kept keys
+    unsigned *s_obj = smem + padded<T>();    // [padded T]: kept objects
+    __shared__ unsigned s_tmp[BLOCK / 32];
+    __shared__ unsigned s_tile;
+    __shared__ unsigned long long s_excl;
+    const int tid = threadIdx.x;
+    // tiles in ticket order, so every tile a look-back waits for has started
+    if (tid == 0) s_tile = atomicAdd(&a.ctl->tickets[7], 1u);
+    __syncthreads();
+    const unsigned t = s_tile;
+    const unsigned ntiles = (a.count + T - 1) / T;
+    const unsigned j0 = t * (unsigned)T;
+    const unsigned cnt = min((unsigned)T, a.count - j0);
+    const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
+    unsigned keys[ITEMS], objs[ITEMS];
+    gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, MeshTab{}, keys, objs);
+    __syncthreads();   // every thread is done with the object marks
+    // the thread's own items, for a test loop that is not unrolled (one copy
+    // of the test instead of ITEMS)
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        s_mark[pad32(tid * ITEMS + i)] = keys[i];
+        s_obj[pad32(tid * ITEMS + i)] = objs[i];
+    }
+    const float lo[3] = {a.lo[0], a.lo[1], a.lo[2]}, scale[3] = {a.scale[0], a.scale[1], a.scale[2]};
+    const unsigned rxy = a.res_x * a.res_y;
+    GridTri tri;
+    unsigned cur = 0xFFFFFFFFu, mask = 0u;
+#pragma unroll 1
+    for (int i = 0; i < ITEMS; ++i) {
+        const unsigned e = tid * ITEMS + i;
+        if (e >= cnt) break;
+        const unsigned o = s_obj[pad32(e)], key = s_mark[pad32(e)];
+        if (o != cur) {
+            cur = o;
+            grid_tri(a.verts, a.nverts, a.tris, cur, lo, scale, tri, a.ctl);
+        }
+        const unsigned z = key / rxy;
+        const unsigned rem = key - z * rxy;
+        const unsigned y = rem / a.res_x;
+        const unsigned x = rem - y * a.res_x;
+        if (!tri_cell_separated(tri, x, y, z)) mask |= 1u << i;
+    }
+    unsigned total;
+    // ends with a barrier: every thread has read its items, the arrays are free
+    unsigned pos = block_excl_sum<BLOCK>((unsigned)__popc(mask), s_tmp, &total);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if ((mask >> i) & 1u) {
+            s_mark[pad32(pos)] = keys[i];
+            s_obj[pad32(pos)] = objs[i];
+            ++pos;
+        }
+    }
+    if (tid == 0) {
+        unsigned long long *st = a.status;
+        unsigned long long excl = 0;
+        if (t == 0) {
+            st_relaxed_u64(&st[0], LB64_PREFIX | total);
+        } else {
+            st_relaxed_u64(&st[t], LB64_AGG | total);
+            long long k = (long long)t - 1;
+            unsigned spins = 0;
+            while (k >= 0) {
+                const unsigned long long v = ld_relaxed_u64(&st[k]);
+                if (v == 0ull) {
+                    if (++spins > SPIN_LIMIT) {
+                        atomicOr(&a.ctl->err, ERR_TIMEOUT);
+                        break;
+                    }
+                    if (spins > 8) __nanosleep(64);
+                    continue;
+                }
+                excl += v & LB64_VALUE;
+                if (v & LB64_PREFIX) break;
+                --k;
+            }
+            st_relaxed_u64(&st[t], LB64_PREFIX | ((excl + total) & LB64_VALUE));
+        }
+        s_excl = excl;
+        if (t == ntiles - 1) a.ctl->nkept = excl + total;
+    }
+    __syncthreads();
+    const unsigned long long base = s_excl;
+    for (unsigned e = tid; e < total; e += BLOCK) {
+        const unsigned long long d = base + e;
+        if (d < a.count) {   // always true for consistent records; never write past the buffers
+            a.C[d] = s_mark[pad32(e)];
+            a.O[d] = s_obj[pad32(e)];
+        } else {
+            atomicOr(&a.ctl->err, ERR_RANGE);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // a8: RadixSort(C, O) - stable LSD passes, each an upsweep and a downsweep
 // ---------------------------------------------------------------------------
 //
@@ -1143,6 +1332,18 @@ cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s)
     if (a.count == 0) return cudaSuccess;
     const unsigned tiles = (a.count + PAIR_TILE - 1) / PAIR_TILE;
     auto k = emit_kernel<PAIR_BLOCK, PAIR_TILE / PAIR_BLOCK>;
+    const size_t smem = 2 * sizeof(unsigned) * padded<PAIR_TILE>();
+    static std::atomic<unsigned long long> configured{0};
+    if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
+    k<<<tiles, PAIR_BLOCK, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cull_emit(const CullArgs &a, cudaStream_t s)
+{
+    if (a.count == 0) return cudaSuccess;
+    const unsigned tiles = (a.count + PAIR_TILE - 1) / PAIR_TILE;
+    auto k = cull_emit_kernel<PAIR_BLOCK, PAIR_TILE / PAIR_BLOCK>;
     const size_t smem = 2 * sizeof(unsigned) * padded<PAIR_TILE>();
     static std::atomic<unsigned long long> configured{0};
     if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;

@@ -79,6 +79,23 @@ struct EmitArgs {
     unsigned *O;
 };
 
+// Culling emit: the object-order pairs of the box placement minus those the
+// triangle/cell separating-axis test rejects, compacted in object order.
+struct CullArgs {
+    const ObjRec *recs;
+    const unsigned *tile_obj;       // [ntiles + 1]
+    const float *verts;
+    long long nverts;
+    const int *tris;
+    float lo[3], scale[3];
+    unsigned res_x, res_y;
+    unsigned count;                 // NO of the box placement
+    unsigned *C;                    // [count] out, first nkept entries used
+    unsigned *O;
+    unsigned long long *status;     // [ntiles] look-back words, zero on entry
+    Ctl *ctl;                       // nkept out
+};
+
 // Upsweep of one radix-sort pass: digit counts per tile, offsets of each
 // tile inside its group of GROUP_TILES tiles, offsets of each group.  With
 // with_hist it also counts the digits of every pass and writes the digit
@@ -162,6 +179,7 @@ cudaError_t launch_count_scan(const CountArgs &a, cudaStream_t s);
 cudaError_t launch_tile_search(const ObjRec *recs, long long n, unsigned tile, unsigned ntiles,
                                unsigned *tile_obj, cudaStream_t s);
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s);
+cudaError_t launch_cull_emit(const CullArgs &a, cudaStream_t s);
 // Pair-generation ablation (sorted_grid.cu): one thread per object writes its
 // pairs C[start ..], O[start ..] (single mesh).
 cudaError_t launch_make_pairs_per_object(const ObjRec *recs, long long n, unsigned res_x, unsigned res_y,

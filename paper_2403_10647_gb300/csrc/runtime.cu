@@ -45,11 +45,12 @@ struct Scratch {
 
 enum KernelId {
     K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_LOCALIZE,
-    K_PER_OBJECT, K_NUM
+    K_PER_OBJECT, K_CULL, K_NUM
 };
 const char *const kKernelNames[K_NUM] = {"bounds",  "count_scan",    "tile_search",   "emit",
                                          "upsweep_gen", "downsweep_gen", "upsweep", "downsweep",
-                                         "extract_split", "extract",   "localize", "make_pairs_per_object"};
+                                         "extract_split", "extract",   "localize", "make_pairs_per_object",
+                                         "cull_emit"};
 
 struct PendingTiming {
     int kid;
@@ -67,6 +68,7 @@ struct grid_ctx {
     grid_opts opts{};
     int rbits_max = 9;
     int pair_gen = GRID_PAIRS_FUSED;
+    bool cull = false;
 
     Ctl *d_ctl = nullptr;        // device control block
     Ctl *h_ctl = nullptr;        // pinned host mirror
@@ -76,7 +78,8 @@ struct grid_ctx {
     Scratch recs, k2status, tile_obj, keys_sorted, keys[1], vals[1], intra, gpref, gstatus, splits;
     Scratch in_verts, in_tris, out_cells, out_refs;  // host-buffer builds
     Scratch b_desc, b_base, b_state, b_pairbase, b_cellsoff, b_G;   // batched builds
-    Scratch pairs_C, pairs_O;    // object-order pairs of the unfused pair_gen modes
+    Scratch pairs_C, pairs_O;    // object-order pairs of the unfused pair_gen modes and of culling
+    Scratch cstatus;             // culling emit look-back words
     std::atomic<int64_t> in_use{0};
 
     // per-kernel accounting
@@ -415,6 +418,51 @@ struct OutAlloc {
     virtual ~OutAlloc() = default;
 };
 
+// Culling emit over the box placement's NO pairs: the kept pairs, compacted
+// in object order, into C / O; *nkept from the device (synchronises).
+int cull_pairs(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *tris, const grid_info &I,
+               const ObjRec *recs, int64_t n, int64_t NO, unsigned *C, unsigned *O, int64_t *nkept)
+{
+    *nkept = 0;
+    if (NO == 0) return GRID_OK;
+    const unsigned ntiles = pair_tiles(NO);
+    GG_TRY(ensure(c, c->tile_obj, (size_t)(ntiles + 1) * sizeof(unsigned)));
+    {
+        KernelScope ks(c, K_TILES, 4.0 * (ntiles + 1));
+        GG_CUDA(gg::launch_tile_search(recs, n, gg::PAIR_TILE, ntiles, (unsigned *)c->tile_obj.ptr, c->stream));
+    }
+    GG_TRY(ensure(c, c->cstatus, (size_t)ntiles * 8));
+    GG_CUDA(cudaMemsetAsync(c->cstatus.ptr, 0, (size_t)ntiles * 8, c->stream));
+    GG_CUDA(cudaMemsetAsync(&c->d_ctl->tickets[7], 0, sizeof(unsigned), c->stream));
+    gg::CullArgs ca{};
+    ca.recs = recs;
+    ca.tile_obj = (const unsigned *)c->tile_obj.ptr;
+    ca.verts = verts;
+    ca.nverts = nverts;
+    ca.tris = tris;
+    for (int a = 0; a < 3; ++a) {
+        ca.lo[a] = I.lo[a];
+        ca.scale[a] = I.scale[a];
+    }
+    ca.res_x = (unsigned)I.res[0];
+    ca.res_y = (unsigned)I.res[1];
+    ca.count = (unsigned)NO;
+    ca.C = C;
+    ca.O = O;
+    ca.status = (unsigned long long *)c->cstatus.ptr;
+    ca.ctl = c->d_ctl;
+    {
+        // reads the records and the triangles' vertices, writes the kept pairs
+        // (counted at the box placement's NO: the bytes it may write)
+        KernelScope ks(c, K_CULL, 16.0 * n + 48.0 * n + 8.0 * NO);
+        GG_CUDA(gg::launch_cull_emit(ca, c->stream));
+    }
+    GG_TRY(read_ctl(c));
+    GG_TRY(ctl_error(c->h_ctl->err));
+    *nkept = (int64_t)c->h_ctl->nkept;
+    return GRID_OK;
+}
+
 // BuildParallelGrid (Algorithm 1) on device-resident inputs.
 int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
                float lambda, grid_info *info, OutAlloc &out)
@@ -474,6 +522,38 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
     const int64_t NO = (int64_t)c->h_ctl->nrefs;
     if (NO > kInt32Max) return GRID_EOVERFLOW;
     I.nrefs = NO;
+
+    if (c->cull) {
+        // the box pairs minus the culled ones, in object order, then the
+        // in-memory sort and the range steps over the kept pairs
+        GG_TRY(ensure(c, c->pairs_C, (size_t)std::max<int64_t>(NO, 1) * sizeof(unsigned)));
+        GG_TRY(ensure(c, c->pairs_O, (size_t)std::max<int64_t>(NO, 1) * sizeof(unsigned)));
+        unsigned *C = (unsigned *)c->pairs_C.ptr, *O = (unsigned *)c->pairs_O.ptr;
+        int64_t NK = 0;
+        GG_TRY(cull_pairs(c, verts, nverts, tris, I, (const ObjRec *)c->recs.ptr, n, NO, C, O, &NK));
+        I.nrefs = NK;
+        GG_TRY(out.alloc(c, I.ncells + 1, NK, &cells, &refs));
+        if (NK > 0) {
+            const unsigned kc = (unsigned)NK;
+            const SortCfg sc = sort_cfg(I.key_bits, c->rbits_max);
+            const unsigned *keys = C;
+            if (sc.passes == 0) {
+                GG_CUDA(cudaMemcpyAsync(refs, O, (size_t)kc * 4, cudaMemcpyDeviceToDevice, c->stream));
+            } else {
+                GG_TRY(ensure(c, c->keys_sorted, (size_t)kc * sizeof(unsigned)));
+                GG_TRY(sort_pairs(c, sc, kc, false, nullptr, 0, nullptr, 0, 0, gg::MeshTab{}, C, O,
+                                  (unsigned *)c->keys_sorted.ptr, refs));
+                keys = (const unsigned *)c->keys_sorted.ptr;
+            }
+            GG_TRY(extract_ranges(c, keys, kc, I.ncells, cells));
+        } else {
+            GG_CUDA(cudaMemsetAsync(cells, 0, (size_t)(I.ncells + 1) * sizeof(unsigned), c->stream));
+        }
+        GG_TRY(read_ctl(c));
+        GG_TRY(ctl_error(c->h_ctl->err));
+        if (info) *info = I;
+        return GRID_OK;
+    }
 
     GG_TRY(out.alloc(c, I.ncells + 1, NO, &cells, &refs));
     const unsigned count = (unsigned)NO;
@@ -617,6 +697,11 @@ int grid_ctx_create(int device, const grid_opts *opts, grid_ctx **out)
         return GRID_EINVAL;
     }
     c->pair_gen = c->opts.pair_gen;
+    if (c->opts.cull != 0 && c->opts.cull != 1) {
+        delete c;
+        return GRID_EINVAL;
+    }
+    c->cull = c->opts.cull == 1;
     int rc = GRID_OK;
     do {
         if ((rc = cuda_err(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device)))) break;
@@ -657,7 +742,7 @@ void grid_ctx_destroy(grid_ctx *c)
         Scratch *all[] = {&c->recs, &c->k2status, &c->tile_obj, &c->splits, &c->keys_sorted, &c->keys[0],
                           &c->vals[0], &c->intra, &c->gpref, &c->gstatus, &c->in_verts, &c->in_tris,
                           &c->out_cells, &c->out_refs, &c->b_desc, &c->b_base, &c->b_state, &c->b_pairbase,
-                          &c->b_cellsoff, &c->b_G, &c->pairs_C, &c->pairs_O};
+                          &c->b_cellsoff, &c->b_G, &c->pairs_C, &c->pairs_O, &c->cstatus};
         for (Scratch *s : all) release(c, *s);
         if (c->stream) cudaStreamSynchronize(c->stream);
         resolve_timings(c);
@@ -1076,6 +1161,21 @@ int grid_emit_pairs_per_object(grid_ctx *c, const grid_objrec *recs, int64_t n, 
     }
     GG_TRY(read_ctl(c));
     return ctl_error(c->h_ctl->err);
+}
+
+int grid_cull_pairs(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
+                    const grid_info *info, const grid_objrec *recs, int64_t nrefs, int32_t *C, int32_t *O,
+                    int64_t *nkept)
+{
+    if (!c || !info || !nkept || n < 0 || nverts < 0 || nrefs < 0 || nrefs > kInt32Max) return GRID_EINVAL;
+    *nkept = 0;
+    if (nrefs == 0) return GRID_OK;
+    if (n == 0 || !verts || !tris || !recs || !C || !O) return GRID_EINVAL;
+    if (info->res[0] < 1 || info->res[1] < 1 || info->res[2] < 1) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    GG_TRY(reset_ctl(c));
+    return cull_pairs(c, verts, nverts, tris, *info, (const ObjRec *)recs, n, nrefs, (unsigned *)C,
+                      (unsigned *)O, nkept);
 }
 
 int grid_sort_pairs(grid_ctx *c, const int32_t *C, const int32_t *O, int64_t count, int32_t key_bits,
