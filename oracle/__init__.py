@@ -247,11 +247,12 @@ def tri_cell_separated(q, x: int, y: int, z: int) -> bool:
 
 def grid_space(verts, tris, p: Plan):
     """q float32[n, 3, 3]: each triangle's vertices in grid coordinates,
-    (v - lo) * scale with both operations rounded to FP32 (numpy float32
-    arithmetic: one rounding per operation)."""
+    min((v - lo) * scale, res) with each operation rounded to FP32 (numpy
+    float32 arithmetic: one rounding per operation)."""
     v = _c(verts, np.float32, (-1, 3))
     t = _c(tris, np.int32, (-1, 3))
-    return ((v[t] - p.lo[None, None, :]).astype(np.float32) * p.scale[None, None, :]).astype(np.float32)
+    q = ((v[t] - p.lo[None, None, :]).astype(np.float32) * p.scale[None, None, :]).astype(np.float32)
+    return np.minimum(q, p.res.astype(np.float32)[None, None, :])
 
 
 def cull_pairs(verts, tris, p: Plan, clo, chi, cap: int):

@@ -348,9 +348,12 @@ int or_grid_bruteforce(const int32_t *clo, const int32_t *chi, int64_t n, const 
  * paper names a triangle/cell overlap test ahead of the sort as future work.
  * This is that test, with one fixed reading:
  *
- *   grid-space vertex  q_k = (v_k - lo) * scale per axis: the two FP32
- *                      operations of the cell mapping, so floor(q) is the
- *                      vertex's cell;
+ *   grid-space vertex  q_k = min((v_k - lo) * scale, res) per axis: the two
+ *                      FP32 operations of the cell mapping, so floor(q) is
+ *                      the vertex's cell, and the clamp to the grid's far
+ *                      face that the mapping applies to cells (scale =
+ *                      res / e rounded to FP32 can put the far face's vertex
+ *                      up to res 2^-23 beyond res, outside the last cell);
  *   cell (x, y, z)     the closed unit cube centred at c = (x, y, z) + 1/2;
  *   local vertex       w_k = q_k - c;
  *   edges              e_0 = q_1 - q_0, e_1 = q_2 - q_1, e_2 = q_0 - q_2;
@@ -445,7 +448,8 @@ int or_cull_pairs(const float *verts, const int32_t *tris, int64_t n, const floa
         for (int v = 0; v < 3; ++v)
             for (int a = 0; a < 3; ++a) {
                 float t = verts[3 * (int64_t)tris[3 * i + v] + a] - lo[a];
-                q[3 * v + a] = t * scale[a];
+                float u = t * scale[a];
+                q[3 * v + a] = u > (float)res[a] ? (float)res[a] : u;
             }
         const int32_t *l = &clo[3 * i], *h = &chi[3 * i];
         int64_t ki = 0;

@@ -423,6 +423,28 @@ def pin_cull_exact(ntri: int = 150, seed: int = 15):
     assert checked > 1000 and dropped > 100, (checked, dropped)
 
 
+def pin_cull_far_face():
+    """A triangle lying in the grid's far face plane keeps its cells.  With
+    res_x = 61846 over an extent of 804.099365 the FP32 scale puts that plane
+    at grid x = 61846.0039, 0.0039 cells beyond the last cell (more than the
+    test's slack): the clamp of the grid coordinate to res, like the cell
+    mapping's clamp, keeps the triangle in the last cell layer.  In the y-z
+    plane it is the right triangle of the hand case right_x, whose 13 kept
+    cells were worked out by hand."""
+    sc = np.float32(61846) / np.float32(804.099365234375)
+    assert float(np.float32(np.float32(804.099365234375) * sc)) - 61846 > 2.0 ** -9
+    p = hand_plan(lo=(0, 0, 0), scale=(sc, 1, 1), res=(61846, 4, 4))
+    x = np.float32(804.099365234375)
+    verts = np.array([[x, 0.5, 0.5], [x, 3.5, 0.5], [x, 0.5, 3.5]], np.float32)
+    tris = np.array([[0, 1, 2]], np.int32)
+    clo, chi, V = oracle.cell_boxes(verts, tris, p)
+    assert clo[0, 0] == chi[0, 0] == 61845 and V[0] == 16
+    C, O, kept = oracle.cull_pairs(verts, tris, p, clo, chi, int(V[0]))
+    yz = sorted(((int(c) // 61846) % 4, int(c) // (61846 * 4)) for c in C)
+    want = sorted((y, z) for z in range(4) for y in range(4) if y + z <= 4)
+    assert (C % 61846 == 61845).all() and yz == want, (yz, want)
+
+
 def pin_cull_invariants():
     """On scenes: the kept pairs are a subsequence of the box pairs (object
     order, GlobalCoords order inside an object); the cell of every vertex and
@@ -463,7 +485,7 @@ def pin_cull_invariants():
 
 ALL_PINS = [pin_hand_example, pin_fig1_cells, pin_shifted_cells, pin_point_in_cell, pin_plan_cases, pin_plan_errors, pin_bounds,
             pin_bruteforce, pin_brute_boxes, pin_library_routines, pin_invariants,
-            pin_cull_hand, pin_cull_exact, pin_cull_invariants]
+            pin_cull_hand, pin_cull_exact, pin_cull_far_face, pin_cull_invariants]
 
 
 def run_all():

@@ -52,6 +52,7 @@ MUTANTS = {
                                  "for (int k = 0; k < 2; ++k) {\n            float p = a[0]"),
     "cull_normal_component_swapped": ("ax[0][1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];",
                                       "ax[0][1] = e[0][0] * e[1][2] - e[0][2] * e[1][0];"),
+    "cull_no_far_face_clamp": ("q[3 * v + a] = u > (float)res[a] ? (float)res[a] : u;", "q[3 * v + a] = u;"),
     "place_reversed": ("for (int64_t j = 0; j < NO; ++j) refs[cnt[C[j]]++] = O[j];",
                        "for (int64_t j = NO - 1; j >= 0; --j) refs[cnt[C[j]]++] = O[j];"),
 }
