@@ -53,7 +53,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="the scene one step builds (default: the 10M-triangle architectural scene)")
-    ap.add_argument("--radix-bits", type=int, default=0)
+    ap.add_argument("--radix-bits", type=int, default=0,
+                    help="fix the radix digit width (8..11) instead of autotuning it")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--cull", action="store_true",
+                    help="time the culled build (false-intersection culling before the sort) instead")
+    ap.add_argument("--pair-gen", default=None, choices=["fused", "regen", "emit", "per_object"],
+                    help="fix the pair generation instead of autotuning it")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -61,6 +67,20 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
+
+
+def reduce_job(units: float, seconds: float, dist=None, device=None):
+    """Whole-job totals over the ranks: the units every rank processed,
+    summed, and the slowest rank's time (max).  Without a process group the
+    values pass through."""
+    if dist is None:
+        return float(units), float(seconds)
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
 
 
 def dist_env():
@@ -246,18 +266,19 @@ def bench_batched(ctx, scale: float, reps: int = 5):
 
 
 def bench_pair_gen(scene, reps: int = 5):
-    """Pair-generation ablation on one scene: the default fused path (pairs
-    generated inside the first sort pass), the paper's unfused chain (pairs
-    written to device memory by one thread per pair, then sorted) and the
-    sorted grid's one-thread-per-object MakePairs, each timed per build with
-    CUDA events and per kernel with the library's own event accounting."""
+    """Pair-generation ablation on one scene: the default (pairs generated by
+    the first sort pass's counting kernel and stored once), the first pass
+    regenerating them in both of its kernels, the paper's unfused chain (a
+    kernel of its own writes them, then the sort) and the sorted grid's
+    one-thread-per-object MakePairs, each timed per build with CUDA events
+    and per kernel with the library's own event accounting."""
     import torch
     import paper_2403_10647_gb300 as pg
     v = torch.from_numpy(scene.verts).cuda()
     t = torch.from_numpy(scene.tris).cuda()
     out = {"n_tris": scene.n}
     ref = None
-    for mode in ("fused", "emit", "per_object"):
+    for mode in ("fused", "regen", "emit", "per_object"):
         c = pg.Context(0, pair_gen=mode)
         try:
             g = c.build(v, t, scene.lam)
@@ -280,8 +301,8 @@ def bench_pair_gen(scene, reps: int = 5):
             torch.cuda.synchronize()
             st = c.kernel_stats()
             c.profile(False)
-            gen = {"fused": ("upsweep_gen", "downsweep_gen"), "emit": ("tile_search", "emit"),
-                   "per_object": ("make_pairs_per_object",)}[mode]
+            gen = {"fused": ("upsweep_gen",), "regen": ("upsweep_gen", "downsweep_gen"),
+                   "emit": ("tile_search", "emit"), "per_object": ("make_pairs_per_object",)}[mode]
             out[mode] = {"ms_per_build": e0.elapsed_time(e1) / reps,
                          "pair_generation_ms": sum(st[k]["ms"] for k in gen if k in st) / reps,
                          "pair_generation_kernels": list(gen)}
@@ -447,11 +468,14 @@ def run_ours(args, rank, world, local):
             dist.barrier()
 
     scene = make_scene(args.workload)
-    ctx = pg.Context(local, radix_bits=args.radix_bits)
+    ctx = pg.Context(local, radix_bits=args.radix_bits, pair_gen=args.pair_gen or "fused", cull=args.cull)
     v = torch.from_numpy(scene.verts).cuda()
     t = torch.from_numpy(scene.tris).cuda()
     torch.cuda.synchronize()
 
+    tuned = None
+    if not args.no_autotune and not args.radix_bits and not args.pair_gen:
+        tuned = ctx.autotune(v, t, scene.lam, reps=3)   # before the timed region
     for _ in range(max(args.warmup, 3)):
         g = ctx.build(v, t, scene.lam)
         del g
@@ -475,11 +499,9 @@ def run_ours(args, rank, world, local):
     ms = e0.elapsed_time(e1)
     stats = ctx.kernel_stats()
     ctx.profile(False)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = nrefs * args.steps * world / (ms_max / 1e3)
+    units, sec_max = reduce_job(nrefs * args.steps, ms / 1e3, dist, "cuda")
+    ms_max = sec_max * 1e3
+    value = units / sec_max
 
     # ---- end to end through the host-buffer entry point ------------------------------
     e2e = None
@@ -497,11 +519,8 @@ def run_ours(args, rank, world, local):
             ctx.build_host(hv, ht, scene.lam, hc, hr)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        dt_t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
-        dt = float(dt_t.item())
-        e2e = {"value": nrefs * args.steps * world / dt, "unit": METRIC,
+        e2e_units, dt = reduce_job(nrefs * args.steps, dt, dist, "cuda")
+        e2e = {"value": e2e_units / dt, "unit": METRIC,
                "h2d_bytes_per_step": int(hv.numel() * 4 + ht.numel() * 4),
                "d2h_bytes_per_step": int((info.ncells + 1 + nrefs) * 4),
                "ms_per_step": 1e3 * dt / args.steps}
@@ -560,7 +579,12 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "n_tris": scene.n, "lambda": scene.lam, "grid": list(info.res),
                    "ncells": info.ncells, "nrefs": nrefs, "key_bits": info.key_bits,
-                   "radix_bits": args.radix_bits or 9, "l2": l2_note,
+                   "radix_bits": tuned["radix_bits"] if tuned else (args.radix_bits or 9),
+                   "pair_gen": tuned["pair_gen"] if tuned else (args.pair_gen or "fused"),
+                   "cull": bool(args.cull),
+                   "autotune_ms": ({f"{rb}/{m}": round(ms, 4) for (rb, m), ms in tuned["times_ms"].items()}
+                                   if tuned else None),
+                   "l2": l2_note,
                    "parallelism": f"replicas{world}"},
         "builds_per_s": world * args.steps / (ms_max / 1e3),
         "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,

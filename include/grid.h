@@ -92,12 +92,15 @@ typedef struct {
 
 /* How grid_build produces the object-order pairs (C, O) of MakeObjectIds ..
  * MakeCellIds.  The pairs, and so the grid, are the same in every mode. */
-#define GRID_PAIRS_FUSED 0       /* one thread per pair, inside the first radix-sort pass; (C, O)
-                                    never reach device memory (default) */
-#define GRID_PAIRS_EMIT 1        /* one thread per pair, written to device memory, then sorted
-                                    (the paper's chain of separate steps) */
+#define GRID_PAIRS_FUSED 0       /* one thread per pair, generated by the first radix-sort pass's
+                                    counting kernel, which stores them once for the pass's scatter
+                                    to read (default) */
+#define GRID_PAIRS_EMIT 1        /* one thread per pair, written to device memory by a kernel of its
+                                    own, then sorted (the paper's chain of separate steps) */
 #define GRID_PAIRS_PER_OBJECT 2  /* ablation: one thread per object writes all its pairs (the
                                     sorted grid's MakePairs, Sec. 2), then sorted */
+#define GRID_PAIRS_REGEN 3       /* one thread per pair, generated again by each kernel of the first
+                                    radix-sort pass, so (C, O) never reach device memory */
 
 /* Tuning knobs; zero means "library default / autotuned". */
 typedef struct {
@@ -135,6 +138,19 @@ typedef struct {
     double total_ms;      /* sum of event-timed durations (0 when profiling is off) */
     double bytes;         /* sum of algorithmic bytes */
 } grid_kernel_stat;
+
+/* Autotuner: builds the given mesh (device pointers, as grid_build) with
+ * every candidate configuration - radix digits of 8, 9, 10 and 11 bits,
+ * pair generation GRID_PAIRS_FUSED and GRID_PAIRS_EMIT - times each with
+ * CUDA events on the context's stream (median of `reps` builds after one
+ * warm-up; reps <= 0 means 3) and keeps the fastest for the context's later
+ * builds.  Every candidate gives the same grid, so tuning changes speed
+ * only.  *chosen (may be NULL) gets the kept radix_bits and pair_gen; times
+ * (may be NULL, 8 entries) the median ms of each candidate in the order
+ * radix 8..11 x (FUSED, EMIT).  The culling setting is left as it is.
+ * Errors as grid_build; on error the context keeps its previous setting. */
+int grid_ctx_autotune(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
+                      float lambda, int32_t reps, grid_opts *chosen, double *times);
 
 /* Turns event timing on (1) or off (0) and clears the statistics. */
 int grid_ctx_profile(grid_ctx *ctx, int enable);
@@ -236,8 +252,9 @@ int grid_emit_pairs_per_object(grid_ctx *ctx, const grid_objrec *recs, int64_t n
  * grid_count_scan, writes the object-order pairs of the box placement that a
  * triangle/cell test keeps, compacted in the same order, into C and O (int32,
  * capacity nrefs = the box placement's NO); *nkept gets their number
- * (synchronises).  The test, in grid coordinates q = (v - lo) * scale (the
- * cell mapping's two FP32 operations): cell (x, y, z) is the closed unit cube
+ * (synchronises).  The test, in grid coordinates q = min((v - lo) * scale,
+ * res) (the cell mapping's two FP32 operations and its clamp to the far face):
+ * cell (x, y, z) is the closed unit cube
  * centred at c = (x, y, z) + 1/2; with w_k = q_k - c, edges e_0 = q_1 - q_0,
  * e_1 = q_2 - q_1, e_2 = q_0 - q_2, axes n = e_0 x e_1 and (0, -e_z, e_y),
  * (e_z, 0, -e_x), (-e_y, e_x, 0) for each edge, projections
@@ -245,8 +262,10 @@ int grid_emit_pairs_per_object(grid_ctx *ctx, const grid_objrec *recs, int64_t n
  * slack t = max|w| * 2^-16 + 2^-10, a cell is dropped iff for some axis
  * min p > S/2 + S t or max p < -(S/2 + S t), each operation one FP32
  * round-to-nearest step in that order.  The slack exceeds the rounding error,
- * so a triangle touching the cell always keeps it.  GRID_EINVAL for a vertex
- * index outside [0, nverts). */
+ * so a triangle touching the cell always keeps it.  A triangle whose box has at
+ * most two cells keeps them without a test (each holds a vertex), so its
+ * vertices are not read.  GRID_EINVAL if a tested triangle has a vertex index
+ * outside [0, nverts); no vertex is read out of range. */
 int grid_cull_pairs(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
                     const grid_info *info, const grid_objrec *recs, int64_t nrefs, int32_t *C, int32_t *O,
                     int64_t *nkept);

@@ -83,7 +83,7 @@ class Context:
     """A grid-builder context on one CUDA device (C: grid_ctx)."""
 
     PAIR_GEN = {"fused": _lib.GRID_PAIRS_FUSED, "emit": _lib.GRID_PAIRS_EMIT,
-                "per_object": _lib.GRID_PAIRS_PER_OBJECT}
+                "per_object": _lib.GRID_PAIRS_PER_OBJECT, "regen": _lib.GRID_PAIRS_REGEN}
 
     def __init__(self, device: int = 0, radix_bits: int = 0, pair_gen: str = "fused", cull: bool = False):
         import torch
@@ -128,6 +128,27 @@ class Context:
         if not buf.ptr:
             return torch.zeros(int(buf.count), dtype=torch.int32, device=self.device)
         return torch.as_tensor(_LibBuffer(self, buf), device=self.device)
+
+    def autotune(self, verts, tris, lam: float, reps: int = 3) -> dict:
+        """Times every radix width (8..11) x pair generation (fused, emit) on
+        this mesh and keeps the fastest for later builds (same grid either
+        way).  Returns {"radix_bits", "pair_gen", "times_ms": {(bits, mode): ms}}."""
+        torch = self._torch
+        v = self._dev(verts, torch.float32, 3)
+        t = self._dev(tris, torch.int32, 3)
+        self._bind_stream()
+        chosen = GridOpts()
+        times = (ctypes.c_double * 8)()
+        check(self._lib.grid_ctx_autotune(self._h, v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], float(lam),
+                                          int(reps), ctypes.byref(chosen), times), "grid_ctx_autotune")
+        names = {v: k for k, v in self.PAIR_GEN.items()}
+        tt = {}
+        k = 0
+        for rb in range(8, 12):
+            for mode in ("fused", "emit"):
+                tt[(rb, mode)] = float(times[k])
+                k += 1
+        return {"radix_bits": int(chosen.radix_bits), "pair_gen": names[int(chosen.pair_gen)], "times_ms": tt}
 
     def profile(self, enable: bool = True) -> None:
         """Per-kernel CUDA-event timing on (clears the statistics)."""

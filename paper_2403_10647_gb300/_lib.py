@@ -22,6 +22,7 @@ GRID_RES_MAX = 65535
 GRID_PAIRS_FUSED = 0
 GRID_PAIRS_EMIT = 1
 GRID_PAIRS_PER_OBJECT = 2
+GRID_PAIRS_REGEN = 3
 
 c_int32, c_int64, c_float, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
 P = ctypes.POINTER
@@ -81,6 +82,8 @@ SIGNATURES = {
     "grid_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "grid_version": (ctypes.c_char_p, []),
     "grid_ctx_profile": (c_int32, [c_void_p, ctypes.c_int]),
+    "grid_ctx_autotune": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_float, c_int32, P(GridOpts),
+                                    P(ctypes.c_double)]),
     "grid_ctx_kernel_stats": (c_int32, [c_void_p, c_void_p, ctypes.c_int, P(ctypes.c_int)]),
     "grid_build": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_float, P(GridBuf), P(GridBuf),
                              P(GridInfo)]),

@@ -70,23 +70,26 @@ def build_library(force: bool = False, verbose_ptxas: bool = False, out: str | N
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
-    objs = [o for o, _ in results]
-    if verbose_ptxas:
-        for _, log in results:
-            print(log)
-    tmp = target + f".tmp{pid}"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    for o in objs:
-        try:
-            os.remove(o)
-        except OSError:
-            pass
-    if r.returncode != 0:
-        raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, target)
+    tag = abs(hash((target, defines))) % 10**8
+    objs = [os.path.join(BUILD_DIR, f"{os.path.splitext(src)[0]}.{pid}.{tag}.o") for src in SOURCES]
+    try:
+        with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
+            results = list(ex.map(compile_one, SOURCES))
+        if verbose_ptxas:
+            for _, log in results:
+                print(log)
+        tmp = target + f".tmp{pid}"
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, target)
+    finally:
+        for o in objs:   # the objects of a failed build too
+            try:
+                os.remove(o)
+            except OSError:
+                pass
     return target
 
 

@@ -305,12 +305,10 @@ __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
     const unsigned tile = s_tile;
     const long long base = (long long)tile * T;
 
-    uint4 rec[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const long long o = base + i * BLOCK + tid;
         unsigned V = 0u;
-        rec[i] = make_uint4(0u, 0u, 0u, 0u);
         if (o < a.n) {
             // the triangle and the grid it maps into: the single mesh's, or
             // in a batched build the owning mesh's
@@ -359,9 +357,10 @@ __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
                                      (unsigned long long)(chi[1] - clo[1] + 1u) *
                                      (unsigned long long)(chi[2] - clo[2] + 1u);
             V = cnt > 0x80000000ull ? 0x80000000u : (unsigned)cnt;
-            rec[i].x = clo[0] | (clo[1] << 16);
-            rec[i].y = clo[2] | (chi[0] << 16);
-            rec[i].z = chi[1] | (chi[2] << 16);
+            // the box now, the pair offset once the scan has it: nothing
+            // of the record stays live across the scan
+            reinterpret_cast<uint4 *>(a.recs)[o] =
+                make_uint4(clo[0] | (clo[1] << 16), clo[2] | (chi[0] << 16), chi[1] | (chi[2] << 16), 0u);
         }
         s_pref[i * BLOCK + tid] = V;
     }
@@ -413,12 +412,11 @@ __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
     for (int i = 0; i < ITEMS; ++i) {
         const long long o = base + i * BLOCK + tid;
         if (o < a.n) {
-            uint4 r = rec[i];
-            r.w = (unsigned)(excl + s_pref[i * BLOCK + tid]);
-            reinterpret_cast<uint4 *>(a.recs)[o] = r;
+            const unsigned start = (unsigned)(excl + s_pref[i * BLOCK + tid]);
+            a.recs[o].start = start;
             if (a.mt.md) {
                 const int m = mesh_of(a.mt, o);
-                if (__ldg(a.mt.obj_base + m) == o) a.pair_base[m] = r.w;
+                if (__ldg(a.mt.obj_base + m) == o) a.pair_base[m] = start;
             }
         }
     }
@@ -500,9 +498,12 @@ struct GridTri {
     float n[3];
 };
 
+// Grid coordinates q = min((v - lo) * scale, res): the cell mapping's two
+// FP32 operations and its clamp to the grid's far face (the FP32 scale can put
+// the far face's vertices a rounding error beyond res).
 __device__ __forceinline__ void grid_tri(const float *__restrict__ verts, long long nverts,
                                          const int *__restrict__ tris, unsigned o, const float (&lo)[3],
-                                         const float (&scale)[3], GridTri &t, Ctl *ctl)
+                                         const float (&scale)[3], const float (&resf)[3], GridTri &t, Ctl *ctl)
 {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -513,7 +514,7 @@ __device__ __forceinline__ void grid_tri(const float *__restrict__ verts, long l
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            t.q[3 * k + a] = __fmul_rn(__fsub_rn(__ldg(verts + 3ll * vi + a), lo[a]), scale[a]);
+            t.q[3 * k + a] = fminf(__fmul_rn(__fsub_rn(__ldg(verts + 3ll * vi + a), lo[a]), scale[a]), resf[a]);
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -545,12 +546,36 @@ __device__ __forceinline__ bool axis_separates(float a0, float a1, float a2, con
     return pmin > R || pmax < -R;
 }
 
+// Axes that can separate a cell of the triangle's cell box: bit 0 the
+// normal, bit 1 + 3 j + f the f-th cross product with edge j.  An axis with
+// at most one non-zero component is parallel to a coordinate axis; along it
+// the triangle's extent meets the cell's (the cell lies in the box), so the
+// vertex projections nearest the cell stay within S / 2 of its centre
+// (rounding included) while the test needs them beyond S / 2 + S t: such an
+// axis never separates and is skipped without changing any decision.
+__device__ __forceinline__ unsigned live_axes(const GridTri &t)
+{
+    auto two = [](float a, float b, float c) {
+        return (a != 0.0f ? 1 : 0) + (b != 0.0f ? 1 : 0) + (c != 0.0f ? 1 : 0) >= 2;
+    };
+    unsigned m = two(t.n[0], t.n[1], t.n[2]) ? 1u : 0u;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float ex = t.e[3 * j], ey = t.e[3 * j + 1], ez = t.e[3 * j + 2];
+        if (ez != 0.0f && ey != 0.0f) m |= 2u << (3 * j);
+        if (ez != 0.0f && ex != 0.0f) m |= 4u << (3 * j);
+        if (ey != 0.0f && ex != 0.0f) m |= 8u << (3 * j);
+    }
+    return m;
+}
+
 // The culling test: is triangle t separated from cell (x, y, z), the closed
 // unit cube centred at (x, y, z) + 1/2?  Axes: the normal, then unit x e for
-// every edge; slack t = max|w| 2^-16 + 2^-10 (bounds the rounding error of
-// the projections from above by a wide margin: a touching cell is never
-// rejected).
-__device__ __forceinline__ bool tri_cell_separated(const GridTri &t, unsigned x, unsigned y, unsigned z)
+// every edge (those of `live` only); slack t = max|w| 2^-16 + 2^-10 (bounds
+// the rounding error of the projections from above by a wide margin: a
+// touching cell is never rejected).
+__device__ __forceinline__ bool tri_cell_separated(const GridTri &t, unsigned live, unsigned x, unsigned y,
+                                                   unsigned z)
 {
     const float c[3] = {__fadd_rn(__uint2float_rn(x), 0.5f), __fadd_rn(__uint2float_rn(y), 0.5f),
                         __fadd_rn(__uint2float_rn(z), 0.5f)};
@@ -564,13 +589,13 @@ __device__ __forceinline__ bool tri_cell_separated(const GridTri &t, unsigned x,
             W = fmaxf(W, fabsf(w[3 * k + a]));
         }
     const float slack = __fadd_rn(__fmul_rn(W, 1.52587890625e-05f), 9.765625e-04f);   // 2^-16, 2^-10
-    if (axis_separates(t.n[0], t.n[1], t.n[2], w, slack)) return true;
+    if ((live & 1u) && axis_separates(t.n[0], t.n[1], t.n[2], w, slack)) return true;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const float ex = t.e[3 * j], ey = t.e[3 * j + 1], ez = t.e[3 * j + 2];
-        if (axis_separates(0.0f, -ez, ey, w, slack)) return true;
-        if (axis_separates(ez, 0.0f, -ex, w, slack)) return true;
-        if (axis_separates(-ey, ex, 0.0f, w, slack)) return true;
+        if (((live >> (3 * j)) & 2u) && axis_separates(0.0f, -ez, ey, w, slack)) return true;
+        if (((live >> (3 * j)) & 4u) && axis_separates(ez, 0.0f, -ex, w, slack)) return true;
+        if (((live >> (3 * j)) & 8u) && axis_separates(-ey, ex, 0.0f, w, slack)) return true;
     }
     return false;
 }
@@ -580,8 +605,10 @@ __global__ void __launch_bounds__(BLOCK) cull_emit_kernel(CullArgs a)
 {
     constexpr int T = BLOCK * ITEMS;
     extern __shared__ __align__(16) unsigned smem[];
-    unsigned *s_mark = smem;                 // [padded T]: object marks, then kept keys
-    unsigned *s_obj = smem + padded<T>();    // [padded T]: kept objects
+    unsigned *s_mark = smem;                     // [padded T]: object marks, then the tile's keys
+    unsigned *s_obj = smem + padded<T>();        // [padded T]: the tile's objects
+    unsigned *s_okey = smem + 2 * padded<T>();   // [padded T]: kept keys, compacted
+    unsigned *s_oobj = smem + 3 * padded<T>();   // [padded T]: kept objects, compacted
     __shared__ unsigned s_tmp[BLOCK / 32];
     __shared__ unsigned s_tile;
     __shared__ unsigned long long s_excl;
@@ -594,43 +621,103 @@ __global__ void __launch_bounds__(BLOCK) cull_emit_kernel(CullArgs a)
     const unsigned j0 = t * (unsigned)T;
     const unsigned cnt = min((unsigned)T, a.count - j0);
     const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
-    unsigned keys[ITEMS], objs[ITEMS];
-    gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, MeshTab{}, keys, objs);
-    __syncthreads();   // every thread is done with the object marks
-    // the thread's own items, for a test loop that is not unrolled (one copy
-    // of the test instead of ITEMS)
+    {
+        unsigned keys[ITEMS], objs[ITEMS];
+        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, MeshTab{}, keys, objs);
+        __syncthreads();   // every thread is done with the object marks
+        // the thread's own items go to shared memory: the test loop below is
+        // not unrolled (one copy of the test) and no item stays in registers
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        s_mark[pad32(tid * ITEMS + i)] = keys[i];
-        s_obj[pad32(tid * ITEMS + i)] = objs[i];
+        for (int i = 0; i < ITEMS; ++i) {
+            s_mark[pad32(tid * ITEMS + i)] = keys[i];
+            s_obj[pad32(tid * ITEMS + i)] = objs[i];
+        }
     }
     const float lo[3] = {a.lo[0], a.lo[1], a.lo[2]}, scale[3] = {a.scale[0], a.scale[1], a.scale[2]};
-    const unsigned rxy = a.res_x * a.res_y;
+    const float resf[3] = {a.res_f[0], a.res_f[1], a.res_f[2]};
+    // The thread's items are consecutive pairs: inside one object the cell
+    // steps through the box, x fastest (GlobalCoords), so coordinates are
+    // stepped, not divided out of the key.  Two exact shortcuts skip the
+    // test: a cell holding a vertex of the triangle is always kept (each
+    // vertex projection nearest the cell lies within S / 2 of its centre),
+    // and so is every cell of a box of at most two cells (each holds a vertex).
     GridTri tri;
-    unsigned cur = 0xFFFFFFFFu, mask = 0u;
+    unsigned cur = 0xFFFFFFFFu, mask = 0u, live = 0u;
+    unsigned x = 0, y = 0, z = 0, lox = 0, loy = 0, hix = 0, hiy = 0;
+    unsigned long long vc[3] = {0ull, 0ull, 0ull};   // the vertices' cells, x | y << 16 | z << 32
+    bool small = true;
 #pragma unroll 1
     for (int i = 0; i < ITEMS; ++i) {
         const unsigned e = tid * ITEMS + i;
         if (e >= cnt) break;
-        const unsigned o = s_obj[pad32(e)], key = s_mark[pad32(e)];
+        const unsigned o = s_obj[pad32(e)];
         if (o != cur) {
             cur = o;
-            grid_tri(a.verts, a.nverts, a.tris, cur, lo, scale, tri, a.ctl);
+            const uint4 r = __ldg(reinterpret_cast<const uint4 *>(a.recs) + o);
+            lox = r.x & 0xFFFFu;
+            loy = r.x >> 16;
+            const unsigned loz = r.y & 0xFFFFu;
+            hix = r.y >> 16;
+            hiy = r.z & 0xFFFFu;
+            const unsigned hiz = r.z >> 16;
+            const unsigned mx = hix - lox + 1u, my = hiy - loy + 1u, mz = hiz - loz + 1u;
+            if (i > 0) {   // an object that starts inside the thread's run starts at its first cell
+                x = lox;
+                y = loy;
+                z = loz;
+            } else {       // the thread's first pair may lie anywhere inside its object
+                const unsigned rid = j0 + e - r.w;
+                const unsigned mxy = mx * my;
+                const unsigned zz = rid / mxy, rem = rid - zz * mxy;
+                const unsigned yy = rem / mx;
+                x = lox + (rem - yy * mx);
+                y = loy + yy;
+                z = loz + zz;
+            }
+            small = (unsigned long long)mx * my * mz <= 2ull;
+            if (!small) {
+                grid_tri(a.verts, a.nverts, a.tris, o, lo, scale, resf, tri, a.ctl);
+                live = live_axes(tri);
+                const unsigned bl[3] = {lox, loy, loz}, bh[3] = {hix, hiy, hiz};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    unsigned long long key = 0ull;
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        // the vertex's cell: floor of its (clamped) grid
+                        // coordinate, into the box as the cell mapping
+                        // clamps it; the vertex lies in that closed cell
+                        const float f = floorf(tri.q[3 * k + ax]);
+                        const unsigned cc = f <= (float)bl[ax] ? bl[ax] : (f >= (float)bh[ax] ? bh[ax] : (unsigned)f);
+                        key |= (unsigned long long)cc << (16 * ax);
+                    }
+                    vc[k] = key;
+                }
+            }
+        } else if (++x > hix) {
+            x = lox;
+            if (++y > hiy) {
+                y = loy;
+                ++z;
+            }
         }
-        const unsigned z = key / rxy;
-        const unsigned rem = key - z * rxy;
-        const unsigned y = rem / a.res_x;
-        const unsigned x = rem - y * a.res_x;
-        if (!tri_cell_separated(tri, x, y, z)) mask |= 1u << i;
+        bool keep = small;
+        if (!keep) {
+            const unsigned long long rc =
+                (unsigned long long)x | ((unsigned long long)y << 16) | ((unsigned long long)z << 32);
+            keep = rc == vc[0] || rc == vc[1] || rc == vc[2];
+        }
+        if (!keep) keep = !tri_cell_separated(tri, live, x, y, z);
+        if (keep) mask |= 1u << i;
     }
     unsigned total;
-    // ends with a barrier: every thread has read its items, the arrays are free
     unsigned pos = block_excl_sum<BLOCK>((unsigned)__popc(mask), s_tmp, &total);
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < ITEMS; ++i) {
         if ((mask >> i) & 1u) {
-            s_mark[pad32(pos)] = keys[i];
-            s_obj[pad32(pos)] = objs[i];
+            const unsigned e = pad32(tid * ITEMS + i);
+            s_okey[pad32(pos)] = s_mark[e];
+            s_oobj[pad32(pos)] = s_obj[e];
             ++pos;
         }
     }
@@ -667,8 +754,8 @@ __global__ void __launch_bounds__(BLOCK) cull_emit_kernel(CullArgs a)
     for (unsigned e = tid; e < total; e += BLOCK) {
         const unsigned long long d = base + e;
         if (d < a.count) {   // always true for consistent records; never write past the buffers
-            a.C[d] = s_mark[pad32(e)];
-            a.O[d] = s_obj[pad32(e)];
+            a.C[d] = s_okey[pad32(e)];
+            a.O[d] = s_oobj[pad32(e)];
         } else {
             atomicOr(&a.ctl->err, ERR_RANGE);
         }
@@ -761,6 +848,29 @@ __global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
             unsigned objs[ITEMS];
             const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
             gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
+            if (a.gen_keys) {
+                // store the object-order pairs once, for the first downsweep
+                // to read instead of generating them a second time
+                static_assert(ITEMS % 4 == 0, "16-byte stores of a thread's run");
+#pragma unroll
+                for (int i = 0; i < ITEMS; i += 4) {
+                    const unsigned e = tid * ITEMS + i;
+                    if (e + 3 < cnt) {
+                        __stcg(reinterpret_cast<uint4 *>(a.gen_keys + j0 + e),
+                               make_uint4(keys[i], keys[i + 1], keys[i + 2], keys[i + 3]));
+                        __stcg(reinterpret_cast<uint4 *>(a.gen_vals + j0 + e),
+                               make_uint4(objs[i], objs[i + 1], objs[i + 2], objs[i + 3]));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (e + q < cnt) {
+                                a.gen_keys[j0 + e + q] = keys[i + q];
+                                a.gen_vals[j0 + e + q] = objs[i + q];
+                            }
+                        }
+                    }
+                }
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < ITEMS; i += 4) {
@@ -803,7 +913,7 @@ __global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
         }
         __syncthreads();
         for (int d = tid; d < R; d += BLOCK) {
-            a.intra[(size_t)t * R + d] = s_run[d];
+            a.intra[(size_t)t * R + d] = (unsigned short)s_run[d];
             s_run[d] += s_cnt[d];
             s_cnt[d] = 0u;
         }
@@ -981,14 +1091,14 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
             keys[i] = e < cnt ? __ldcs(a.keys_in + j0 + e) : 0u;
         }
     }
-    for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
     __syncthreads();
 
     // warp-level multisplit, stable in element order (items in order,
     // lanes in order): the lanes holding digit d find each other by
-    // OR-ing their lane bit into a shared mask word for d; the lowest of
-    // them reserves the group's slots in the warp's 16-bit digit count
-    // with one shared atomic, clears the mask word, and the old count is
+    // OR-ing their lane bit into a shared mask word for d (each lane first
+    // zeroes the word it is about to use, so no mask memory is cleared in
+    // bulk); the lowest of them reserves the group's slots in the warp's
+    // 16-bit digit count with one shared atomic, and the old count is
     // broadcast.  BATCH items go through each step together so their
     // shared-memory round trips overlap; the reservations are issued in
     // item order, which keeps the ranks stable.
@@ -1002,8 +1112,12 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
             const unsigned e = w * 32 * ITEMS + (ib + q) * 32 + lane;
             ok[q] = e < cnt;
             d[q] = (keys[ib + q] >> sh) & mk;
-            if (ok[q]) atomicOr(&s_wmask[(q * W + w) * R + d[q]], bit);
+            if (ok[q]) s_wmask[(q * W + w) * R + d[q]] = 0u;
         }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q)
+            if (ok[q]) atomicOr(&s_wmask[(q * W + w) * R + d[q]], bit);
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < BATCH; ++q) peers[q] = ok[q] ? s_wmask[(q * W + w) * R + d[q]] : 0u;
@@ -1015,7 +1129,6 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
                 const unsigned hs = (d[q] & 1u) * 16u;
                 old[q] = (atomicAdd(&s_wh32[(w * R + d[q]) >> 1], (unsigned)__popc(peers[q]) << hs) >> hs) &
                          0xFFFFu;
-                s_wmask[(q * W + w) * R + d[q]] = 0u;
             }
         }
         __syncwarp();
@@ -1065,6 +1178,10 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
             ex += loc[k];
         }
     }
+    __syncthreads();
+    // fold each digit's local start into the warps' offsets, so placing an
+    // element takes one shared lookup (positions < T fit 16 bits)
+    for (int i = tid; i < W * R; i += BLOCK) s_wh[i] = (unsigned short)(s_wh[i] + s_dstart[i & (R - 1)]);
     if (IN != IN_GEN) cp_async_wait_all();
     __syncthreads();
     // stage the tile in shared memory in locally sorted order
@@ -1074,7 +1191,7 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
         if (e < cnt) {
             const unsigned d = (keys[i] >> sh) & mk;
             const unsigned rk = (ranks[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
-            const unsigned pos = s_dstart[d] + s_wh[w * R + d] + rk;
+            const unsigned pos = s_wh[w * R + d] + rk;
             if (pos < cnt)
                 s_elem[pos] = pack_kv(keys[i], s_vin[e]);
             else
@@ -1142,32 +1259,71 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
 {
     constexpr int D = BLOCK * ITEMS;
     __shared__ unsigned s_keys[D];
+    __shared__ unsigned s_g[D];
     const int tid = threadIdx.x;
     const unsigned long long nA = a.count, nB = a.ncells + 1ull;
     const unsigned long long M = nA + nB;
     const unsigned long long d0 = (unsigned long long)blockIdx.x * D;
     const unsigned long long d1 = min(d0 + D, M);
     const unsigned long long i0 = a.splits[blockIdx.x], i1 = a.splits[blockIdx.x + 1];
-    const unsigned long long c0 = d0 - i0, c1 = d1 - i1;
-    const unsigned na = (unsigned)(i1 - i0);
-    for (unsigned k = tid; k < na; k += BLOCK) s_keys[k] = __ldcs(a.keys + i0 + k);
-    __syncthreads();
     // every key before i0 is below c0 and every key from i1 on is at least
-    // c1, so G[c] = i0 + (keys of this block below c): one lower-bound search
-    // in shared memory per cell, consecutive threads on consecutive cells
-    for (unsigned long long c = c0 + tid; c < c1; c += BLOCK) {
-        unsigned lo = 0, len = na;
-        while (len > 0) {
-            const unsigned half = len >> 1;
-            if ((unsigned long long)s_keys[lo + half] < c) {
-                lo += half + 1u;
-                len -= half + 1u;
+    // c1, so G[c] = i0 + (keys of this block below c); cell ids fit 32 bits
+    const unsigned c0 = (unsigned)(d0 - i0), c1 = (unsigned)(d1 - i1);
+    const unsigned na = (unsigned)(i1 - i0), nc = c1 - c0, nd = na + nc;
+    // the block's keys: 16-byte loads over the aligned middle (many bytes in
+    // flight per thread), single words at the ragged ends; nothing outside
+    // [i0, i1) is read
+    {
+        // (a caller's array may start off a 16-byte boundary: then words only)
+        const bool vec = (reinterpret_cast<unsigned long long>(a.keys) & 15ull) == 0ull;
+        const unsigned long long a_lo = (i0 + 3ull) & ~3ull, a_hi = i1 & ~3ull;
+        if (vec && a_lo < a_hi) {
+            const unsigned head = (unsigned)(a_lo - i0), nv = (unsigned)((a_hi - a_lo) >> 2);
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.keys + a_lo);
+            for (unsigned v = tid; v < nv; v += BLOCK) {
+                const uint4 q = __ldcs(src + v);
+                const unsigned k = head + 4u * v;
+                s_keys[k] = q.x;
+                s_keys[k + 1] = q.y;
+                s_keys[k + 2] = q.z;
+                s_keys[k + 3] = q.w;
+            }
+            if (tid < (int)head) s_keys[tid] = __ldcs(a.keys + i0 + tid);
+            const unsigned tail0 = (unsigned)(a_hi - i0);
+            if (tid < (int)(na - tail0)) s_keys[tail0 + tid] = __ldcs(a.keys + a_hi + tid);
+        } else {
+            for (unsigned k = tid; k < na; k += BLOCK) s_keys[k] = __ldcs(a.keys + i0 + k);
+        }
+    }
+    __syncthreads();
+    // each thread merges ITEMS consecutive items of the block's range: one
+    // merge-path search for where its diagonal crosses the keys, then a
+    // sequential walk (a cell takes the count of keys taken before it)
+    const unsigned dt = min((unsigned)(tid * ITEMS), nd);
+    unsigned lo = dt > nc ? dt - nc : 0u, hi = min(dt, na);
+    while (lo < hi) {
+        const unsigned mid = (lo + hi) >> 1;
+        // key mid precedes cell c0 + (dt - mid - 1)?
+        if (s_keys[mid] < c0 + (dt - mid - 1u))
+            lo = mid + 1u;
+        else
+            hi = mid;
+    }
+    unsigned i = lo, c = c0 + (dt - lo);
+    const unsigned end = min(dt + (unsigned)ITEMS, nd);
+#pragma unroll
+    for (int step = 0; step < ITEMS; ++step) {
+        if (i + (c - c0) < end) {
+            if (i < na && s_keys[i] < c) {
+                ++i;
             } else {
-                len = half;
+                s_g[c - c0] = (unsigned)i0 + i;
+                ++c;
             }
         }
-        a.G[c] = (unsigned)(i0 + lo);
     }
+    __syncthreads();
+    for (unsigned k = tid; k < nc; k += BLOCK) a.G[(unsigned long long)c0 + k] = s_g[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -1344,7 +1500,7 @@ cudaError_t launch_cull_emit(const CullArgs &a, cudaStream_t s)
     if (a.count == 0) return cudaSuccess;
     const unsigned tiles = (a.count + PAIR_TILE - 1) / PAIR_TILE;
     auto k = cull_emit_kernel<PAIR_BLOCK, PAIR_TILE / PAIR_BLOCK>;
-    const size_t smem = 2 * sizeof(unsigned) * padded<PAIR_TILE>();
+    const size_t smem = 4 * sizeof(unsigned) * padded<PAIR_TILE>();
     static std::atomic<unsigned long long> configured{0};
     if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
     k<<<tiles, PAIR_BLOCK, smem, s>>>(a);

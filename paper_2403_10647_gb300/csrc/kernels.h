@@ -28,6 +28,7 @@ constexpr int PAIR_BLOCK = GG_PAIR_BLOCK;
 constexpr int PAIR_TILE = GG_PAIR_BLOCK * GG_PAIR_ITEMS;
 constexpr int PASS_MIN_BLOCKS = GG_PASS_MIN_BLOCKS;
 constexpr int GROUP_TILES = GG_GROUP_TILES;   // tiles per upsweep block
+static_assert(GROUP_TILES * PAIR_TILE <= 65536, "tile offsets inside a group fit 16 bits");
 constexpr int EXTRACT_BLOCK = 256;
 constexpr int EXTRACT_TILE = 2048;
 
@@ -88,6 +89,7 @@ struct CullArgs {
     long long nverts;
     const int *tris;
     float lo[3], scale[3];
+    float res_f[3];                 // res per axis as float: grid coordinates are clamped to it
     unsigned res_x, res_y;
     unsigned count;                 // NO of the box placement
     unsigned *C;                    // [count] out, first nkept entries used
@@ -106,13 +108,16 @@ struct UpArgs {
     const unsigned *tile_obj;       // SRC_GEN
     MeshTab mt;                     // SRC_GEN, batched
     unsigned res_x, res_y;          // SRC_GEN
+    unsigned *gen_keys;             // SRC_GEN: if set, the generated pairs are stored here
+    unsigned *gen_vals;             //   (object order, [count] each) for the first downsweep
     unsigned count;
     unsigned ntiles;
     int npasses;                    // with_hist: passes counted; shift[0]/bits[0] = this pass
     int shift[MAX_PASSES];
     int bits[MAX_PASSES];
     int with_hist;
-    unsigned *intra;                // [ntiles][2^RBITS] out: tile offsets inside its group
+    unsigned short *intra;          // [ntiles][2^RBITS] out: tile offsets inside its group
+                                    // (< GROUP_TILES * PAIR_TILE <= 65536)
     unsigned *gpref;                // [ngroups][2^RBITS] out: group offsets
     unsigned *status;               // [ngroups][2^RBITS] look-back words, zero on entry
     unsigned *hist;                 // [MAX_PASSES][MAX_RADIX], zero on entry and exit (with_hist)
@@ -136,7 +141,7 @@ struct DownArgs {
     int shift, bits;
     const unsigned *dbase;          // [2^bits] digit starts of this pass
     const unsigned *gpref;          // from the upsweep
-    const unsigned *intra;          // from the upsweep
+    const unsigned short *intra;    // from the upsweep
     Ctl *ctl;
 };
 

@@ -319,10 +319,13 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
     const unsigned ngroups = (ntiles + gg::GROUP_TILES - 1) / gg::GROUP_TILES;
     const int R = 1 << sc.rbits;
     const size_t elem = (size_t)count * sizeof(unsigned);
-    GG_TRY(ensure(c, c->intra, (size_t)ntiles * R * sizeof(unsigned)));
+    // generated pairs are stored once by the first upsweep unless the first
+    // pass regenerates them in both of its kernels
+    const bool store = gen && c->pair_gen != GRID_PAIRS_REGEN;
+    GG_TRY(ensure(c, c->intra, (size_t)ntiles * R * sizeof(unsigned short)));
     GG_TRY(ensure(c, c->gpref, (size_t)ngroups * R * sizeof(unsigned)));
     GG_TRY(ensure(c, c->gstatus, (size_t)ngroups * R * sizeof(unsigned)));
-    if (sc.passes > 1) {
+    if (sc.passes > 1 || store) {
         GG_TRY(ensure(c, c->keys[0], elem));
         GG_TRY(ensure(c, c->vals[0], elem));
     }
@@ -331,6 +334,15 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         const bool to_last = ((sc.passes - 1 - p) % 2) == 0;
         ko[p] = to_last ? keys_last : (unsigned *)c->keys[0].ptr;
         vo[p] = to_last ? vals_last : (unsigned *)c->vals[0].ptr;
+    }
+    // the stored pairs go to the pair of arrays the first pass does not write
+    unsigned *gk = nullptr, *gv = nullptr;
+    if (store) {
+        const bool first_to_last = ko[0] == keys_last;
+        gk = first_to_last ? (unsigned *)c->keys[0].ptr : keys_last;
+        gv = first_to_last ? (unsigned *)c->vals[0].ptr : vals_last;
+        keys_in = gk;
+        vals_in = gv;
     }
     for (int p = 0; p < sc.passes; ++p) {
         const bool first = p == 0;
@@ -344,6 +356,8 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         u.mt = mt;
         u.res_x = res_x;
         u.res_y = res_y;
+        u.gen_keys = first ? gk : nullptr;
+        u.gen_vals = first ? gv : nullptr;
         u.count = count;
         u.ntiles = ntiles;
         u.with_hist = first ? 1 : 0;
@@ -353,15 +367,17 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
             u.shift[q] = sc.shift[pq < gg::MAX_PASSES ? pq : 0];
             u.bits[q] = sc.bits[pq < gg::MAX_PASSES ? pq : 0];
         }
-        u.intra = (unsigned *)c->intra.ptr;
+        u.intra = (unsigned short *)c->intra.ptr;
         u.gpref = (unsigned *)c->gpref.ptr;
         u.status = (unsigned *)c->gstatus.ptr;
         u.hist = c->d_hist;
         u.dbase = c->d_dbase;
         u.ctl = c->d_ctl;
         const bool gen_up = first && gen;
+        const bool gen_down = gen_up && !store;
         {
-            KernelScope ks(c, gen_up ? K_UP_GEN : K_UP, gen_up ? 16.0 * nobj : 4.0 * count);
+            KernelScope ks(c, gen_up ? K_UP_GEN : K_UP,
+                           gen_up ? 16.0 * nobj + (store ? 8.0 * count : 0.0) : 4.0 * count);
             GG_CUDA(gg::launch_upsweep(u, sc.rbits, gen_up ? gg::SRC_GEN : gg::SRC_MEM, c->stream));
         }
         gg::DownArgs a{};
@@ -379,10 +395,10 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         a.bits = sc.bits[p];
         a.dbase = c->d_dbase + p * gg::MAX_RADIX;
         a.gpref = (const unsigned *)c->gpref.ptr;
-        a.intra = (const unsigned *)c->intra.ptr;
+        a.intra = (const unsigned short *)c->intra.ptr;
         a.ctl = c->d_ctl;
-        KernelScope ks(c, gen_up ? K_DOWN_GEN : K_DOWN, gen_up ? 16.0 * nobj + 8.0 * count : 16.0 * count);
-        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_up ? gg::IN_GEN : gg::IN_PAIR, ntiles, c->nsm, c->stream));
+        KernelScope ks(c, gen_down ? K_DOWN_GEN : K_DOWN, gen_down ? 16.0 * nobj + 8.0 * count : 16.0 * count);
+        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_down ? gg::IN_GEN : gg::IN_PAIR, ntiles, c->nsm, c->stream));
     }
     return GRID_OK;
 }
@@ -443,6 +459,7 @@ int cull_pairs(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
     for (int a = 0; a < 3; ++a) {
         ca.lo[a] = I.lo[a];
         ca.scale[a] = I.scale[a];
+        ca.res_f[a] = (float)I.res[a];
     }
     ca.res_x = (unsigned)I.res[0];
     ca.res_y = (unsigned)I.res[1];
@@ -569,7 +586,7 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
         }
         GG_TRY(ensure(c, c->keys_sorted, (size_t)count * sizeof(unsigned)));
         unsigned *keys_sorted = (unsigned *)c->keys_sorted.ptr;
-        if (sc.passes == 0 || c->pair_gen != GRID_PAIRS_FUSED) {
+        if (sc.passes == 0 || c->pair_gen == GRID_PAIRS_EMIT || c->pair_gen == GRID_PAIRS_PER_OBJECT) {
             // object-order (C, O) in device memory: straight into the outputs
             // when there is nothing to sort, else into scratch for the sort
             unsigned *C = keys_sorted, *O = refs;
@@ -692,7 +709,7 @@ int grid_ctx_create(int device, const grid_opts *opts, grid_ctx **out)
     c->device = device;
     if (opts) c->opts = *opts;
     if (c->opts.radix_bits >= 8 && c->opts.radix_bits <= 11) c->rbits_max = c->opts.radix_bits;
-    if (c->opts.pair_gen < GRID_PAIRS_FUSED || c->opts.pair_gen > GRID_PAIRS_PER_OBJECT) {
+    if (c->opts.pair_gen < GRID_PAIRS_FUSED || c->opts.pair_gen > GRID_PAIRS_REGEN) {
         delete c;
         return GRID_EINVAL;
     }
@@ -819,6 +836,75 @@ int grid_build(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
         grid_buf_free(c, out_refs);
     }
     return rc;
+}
+
+int grid_ctx_autotune(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
+                      float lambda, int32_t reps, grid_opts *chosen, double *times)
+{
+    if (!c) return GRID_EINVAL;
+    if (reps <= 0) reps = 3;
+    if (reps > 64) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    const int saved_rbits = c->rbits_max, saved_pg = c->pair_gen;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return GRID_ECUDA;
+    }
+    const int modes[2] = {GRID_PAIRS_FUSED, GRID_PAIRS_EMIT};
+    double best = -1.0;
+    int best_rbits = saved_rbits, best_pg = saved_pg, k = 0, rc = GRID_OK;
+    for (int rb = 8; rb <= 11 && rc == GRID_OK; ++rb) {
+        for (int mi = 0; mi < 2 && rc == GRID_OK; ++mi, ++k) {
+            c->rbits_max = rb;
+            c->pair_gen = modes[mi];
+            std::vector<float> ms;
+            for (int r = 0; r <= reps && rc == GRID_OK; ++r) {
+                grid_buf cells{}, refs{};
+                cudaEventRecord(e0, c->stream);
+                PoolOut po(&cells, &refs);
+                rc = build_core(c, verts, nverts, tris, n, lambda, nullptr, po);
+                cudaEventRecord(e1, c->stream);
+                grid_buf_free(c, &cells);
+                grid_buf_free(c, &refs);
+                if (rc != GRID_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = GRID_ECUDA;
+                    break;
+                }
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (r > 0) ms.push_back(t);   // the first build of a setting warms it up
+            }
+            if (rc != GRID_OK) break;
+            std::sort(ms.begin(), ms.end());
+            const double med = ms[ms.size() / 2];
+            if (times) times[k] = med;
+            if (best < 0.0 || med < best) {
+                best = med;
+                best_rbits = rb;
+                best_pg = modes[mi];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GRID_OK) {
+        c->rbits_max = saved_rbits;
+        c->pair_gen = saved_pg;
+        return rc;
+    }
+    c->rbits_max = best_rbits;
+    c->pair_gen = best_pg;
+    if (chosen) {
+        std::memset(chosen, 0, sizeof(*chosen));
+        chosen->radix_bits = best_rbits;
+        chosen->pair_gen = best_pg;
+        chosen->cull = c->cull ? 1 : 0;
+    }
+    return GRID_OK;
 }
 
 int grid_build_host(grid_ctx *c, const float *h_verts, int64_t nverts, const int32_t *h_tris, int64_t n,

@@ -78,6 +78,26 @@ def test_cull_hand_cases(ctx):
         assert got == want, (case["name"], got, want)
 
 
+def test_cull_far_face(ctx):
+    """A triangle in the grid's far face plane, whose FP32 grid coordinate
+    lands 0.0039 cells beyond the last cell: it keeps its cells in the last
+    layer, as in the oracle (pin_cull_far_face)."""
+    import paper_2403_10647_gb300 as pg
+    sc = float(np.float32(61846) / np.float32(804.099365234375))
+    info = pg.Info(lo=(0.0, 0.0, 0.0), hi=(804.099365234375, 4.0, 4.0), scale=(sc, 1.0, 1.0), res=(61846, 4, 4),
+                   key_bits=20, ncells=61846 * 16, nrefs=0, n=1)
+    x = 804.099365234375
+    verts = np.array([[x, 0.5, 0.5], [x, 3.5, 0.5], [x, 0.5, 3.5]], np.float32)
+    v, t = dev(verts, torch.float32), dev(np.array([[0, 1, 2]]), torch.int32)
+    recs, nrefs = ctx.count_scan(v, t, info)
+    assert nrefs == 16
+    info.nrefs = nrefs
+    C, O = ctx.cull_pairs(v, t, info, recs, nrefs)
+    C = host(C).astype(np.int64)
+    yz = sorted(((int(c) // 61846) % 4, int(c) // (61846 * 4)) for c in C)
+    assert (C % 61846 == 61845).all() and yz == sorted((y, z) for z in range(4) for y in range(4) if y + z <= 4)
+
+
 @pytest.mark.parametrize("name,make", SCENES, ids=[n for n, _ in SCENES])
 def test_culled_build_matches_oracle(cull_ctx, name, make):
     s = make()
@@ -115,8 +135,10 @@ def test_cull_rejects_bad_index(ctx):
     info = pg.plan(lo, hi, s.n, s.lam)
     recs, nrefs = ctx.count_scan(v, t, info)
     info.nrefs = nrefs
+    # a triangle whose box has more than two cells: its vertices are read
+    i = int(np.flatnonzero(np.diff(np.append(host(recs)[:, 3], nrefs)) > 2)[0])
     bad = t.clone()
-    bad[7, 1] = 10**6
+    bad[i, 1] = 10**6
     with pytest.raises(pg.GridError):
         ctx.cull_pairs(v, bad, info, recs, nrefs)
     C, O = ctx.cull_pairs(v, t, info, recs, nrefs)   # the context is still usable

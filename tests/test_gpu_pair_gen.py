@@ -1,8 +1,9 @@
 """The pair-generation modes of grid_build (grid_opts.pair_gen) against the
 oracle: the paper's unfused chain (pairs written to device memory, then
-sorted) and the sorted grid's one-thread-per-object MakePairs (an ablation)
-must give the same object-order pairs and the same grid as the default fused
-path, bit for bit."""
+sorted), the sorted grid's one-thread-per-object MakePairs (an ablation) and
+the first sort pass that regenerates its pairs in both kernels must give the
+same object-order pairs and the same grid as the default path, bit for
+bit."""
 import numpy as np
 import pytest
 
@@ -13,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-MODES = ["emit", "per_object"]
+MODES = ["emit", "per_object", "regen"]
 
 
 def dev(a, dtype):
@@ -98,3 +99,20 @@ def test_bad_mode_rejected():
     o.pair_gen = 7
     h = ctypes.c_void_p()
     assert lib.grid_ctx_create(0, ctypes.byref(o), ctypes.byref(h)) == _lib.GRID_EINVAL
+
+
+def test_autotune_keeps_a_valid_setting_and_the_same_grid():
+    import paper_2403_10647_gb300 as pg
+    s = scenes.nonhomogeneous_soup(60_000, seed=407, extent=40.0)
+    v, t = dev(s.verts, torch.float32), dev(s.tris, torch.int32)
+    c = pg.Context(0)
+    try:
+        before = c.build(v, t, s.lam)
+        r = c.autotune(v, t, s.lam, reps=2)
+        assert r["radix_bits"] in (8, 9, 10, 11) and r["pair_gen"] in ("fused", "emit")
+        assert len(r["times_ms"]) == 8 and all(ms > 0 for ms in r["times_ms"].values())
+        assert r["times_ms"][(r["radix_bits"], r["pair_gen"])] == min(r["times_ms"].values())
+        after = c.build(v, t, s.lam)
+        assert torch.equal(before.cells, after.cells) and torch.equal(before.refs, after.refs)
+    finally:
+        c.close()

@@ -152,6 +152,20 @@ def test_extract_ranges(ctx, ncells, count):
     assert np.array_equal(host(G), oracle.ranges(C, ncells))
 
 
+@pytest.mark.parametrize("offset", [1, 2, 3, 4])
+def test_extract_ranges_unaligned_input(ctx, offset):
+    """A caller's sorted keys may start off a 16-byte boundary (a slice of a
+    larger array): the range extraction then reads them word by word."""
+    g = np.random.Generator(np.random.Philox(77 + offset))
+    ncells, count = 300_000, 1_000_003
+    C = np.sort(g.integers(0, ncells, count)).astype(np.int32)
+    full = dev(np.concatenate([np.zeros(offset, np.int32), C]), torch.int32)
+    view = full[offset:]
+    assert (view.data_ptr() % 16 == 0) == (offset == 4)
+    G = ctx.extract_ranges(view, ncells)
+    assert np.array_equal(host(G), oracle.ranges(C, ncells))
+
+
 # ---- whole builds ---------------------------------------------------------------------
 
 def test_tiny_scenes(ctx):
