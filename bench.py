@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS),
                     help="the scene one step builds (default: the 10M-triangle architectural scene)")
-    ap.add_argument("--radix-bits", type=int, default=0,
-                    help="fix the radix digit width (8..11) instead of autotuning it")
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--radix-bits", type=int, default=8,
+                    help="widest radix digit of the timed builds (8..11); 8 is what the autotuner picks on "
+                         "the 10M-triangle scene (27-bit keys: four passes of up to 8 bits)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the live autotuner run reported in config.autotune_ms")
     ap.add_argument("--cull", action="store_true",
                     help="time the culled build (false-intersection culling before the sort) instead")
     ap.add_argument("--pair-gen", default=None, choices=["fused", "regen", "emit", "per_object"],
@@ -155,11 +157,21 @@ def kernels_digest() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def traffic_from_profiles(kernel: str, nrefs: int):
+def sort_passes(key_bits: int, radix_bits: int):
+    """(passes, widest digit of the kernels) of the library's radix sort for
+    keys of key_bits bits with digits of at most radix_bits bits."""
+    if key_bits <= 0:
+        return (0, 8)
+    passes = -(-key_bits // radix_bits)
+    return (passes, max(8, -(-key_bits // passes)))
+
+
+def traffic_from_profiles(kernel: str, digit_bits: int, nrefs: int):
     """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
-    summary profiles/dram_traffic.txt (lines: kernel, DRAM bytes per pair,
-    digest of the kernel source it was measured on), scaled to this launch's
-    pair count; None if no line covers the kernel as it is now."""
+    summary profiles/dram_traffic.txt (lines: kernel, the kernel's digit
+    width, DRAM bytes per pair, digest of the kernel source it was measured
+    on), scaled to this launch's pair count; None if no line covers the
+    kernel as it is now."""
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
             lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
@@ -167,8 +179,8 @@ def traffic_from_profiles(kernel: str, nrefs: int):
         return None
     digest = kernels_digest()
     for fields in lines:
-        if len(fields) >= 3 and fields[0] == kernel and fields[2] == digest:
-            return float(fields[1]) * nrefs
+        if len(fields) >= 4 and fields[0] == kernel and fields[1] == str(digit_bits) and fields[3] == digest:
+            return float(fields[2]) * nrefs
     return None
 
 
@@ -474,8 +486,15 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
 
     tuned = None
-    if not args.no_autotune and not args.radix_bits and not args.pair_gen:
-        tuned = ctx.autotune(v, t, scene.lam, reps=3)   # before the timed region
+    if not args.no_autotune and not args.cull:
+        # the tuner's view of this workload, on a context of its own (the
+        # timed builds use the fixed --radix-bits / --pair-gen setting, the
+        # one the committed profiles were captured with)
+        tctx = pg.Context(local)
+        try:
+            tuned = tctx.autotune(v, t, scene.lam, reps=3)
+        finally:
+            tctx.close()
     for _ in range(max(args.warmup, 3)):
         g = ctx.build(v, t, scene.lam)
         del g
@@ -543,7 +562,7 @@ def run_ours(args, rank, world, local):
     dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches_per_step"])
     tot_bytes = sum(s["bytes"] for s in stats.values())
     tot_ms = sum(s["ms"] for s in stats.values())
-    traffic = traffic_from_profiles(dom, nrefs)
+    traffic = traffic_from_profiles(dom, sort_passes(info.key_bits, args.radix_bits)[1], nrefs)
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
             "frac": kern[dom]["gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,
             "bytes_per_launch": kern[dom]["bytes_per_launch"],
@@ -579,9 +598,9 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "n_tris": scene.n, "lambda": scene.lam, "grid": list(info.res),
                    "ncells": info.ncells, "nrefs": nrefs, "key_bits": info.key_bits,
-                   "radix_bits": tuned["radix_bits"] if tuned else (args.radix_bits or 9),
-                   "pair_gen": tuned["pair_gen"] if tuned else (args.pair_gen or "fused"),
-                   "cull": bool(args.cull),
+                   "radix_bits": args.radix_bits, "sort_passes": sort_passes(info.key_bits, args.radix_bits),
+                   "pair_gen": args.pair_gen or "fused", "cull": bool(args.cull),
+                   "autotune_choice": f"{tuned['radix_bits']}/{tuned['pair_gen']}" if tuned else None,
                    "autotune_ms": ({f"{rb}/{m}": round(ms, 4) for (rb, m), ms in tuned["times_ms"].items()}
                                    if tuned else None),
                    "l2": l2_note,

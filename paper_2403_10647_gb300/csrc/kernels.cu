@@ -1091,14 +1091,14 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
             keys[i] = e < cnt ? __ldcs(a.keys_in + j0 + e) : 0u;
         }
     }
+    for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
     __syncthreads();
 
     // warp-level multisplit, stable in element order (items in order,
     // lanes in order): the lanes holding digit d find each other by
-    // OR-ing their lane bit into a shared mask word for d (each lane first
-    // zeroes the word it is about to use, so no mask memory is cleared in
-    // bulk); the lowest of them reserves the group's slots in the warp's
-    // 16-bit digit count with one shared atomic, and the old count is
+    // OR-ing their lane bit into a shared mask word for d; the lowest of
+    // them reserves the group's slots in the warp's 16-bit digit count
+    // with one shared atomic, clears the mask word, and the old count is
     // broadcast.  BATCH items go through each step together so their
     // shared-memory round trips overlap; the reservations are issued in
     // item order, which keeps the ranks stable.
@@ -1112,12 +1112,8 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
             const unsigned e = w * 32 * ITEMS + (ib + q) * 32 + lane;
             ok[q] = e < cnt;
             d[q] = (keys[ib + q] >> sh) & mk;
-            if (ok[q]) s_wmask[(q * W + w) * R + d[q]] = 0u;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < BATCH; ++q)
             if (ok[q]) atomicOr(&s_wmask[(q * W + w) * R + d[q]], bit);
+        }
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < BATCH; ++q) peers[q] = ok[q] ? s_wmask[(q * W + w) * R + d[q]] : 0u;
@@ -1129,6 +1125,7 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
                 const unsigned hs = (d[q] & 1u) * 16u;
                 old[q] = (atomicAdd(&s_wh32[(w * R + d[q]) >> 1], (unsigned)__popc(peers[q]) << hs) >> hs) &
                          0xFFFFu;
+                s_wmask[(q * W + w) * R + d[q]] = 0u;
             }
         }
         __syncwarp();
@@ -1178,10 +1175,6 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
             ex += loc[k];
         }
     }
-    __syncthreads();
-    // fold each digit's local start into the warps' offsets, so placing an
-    // element takes one shared lookup (positions < T fit 16 bits)
-    for (int i = tid; i < W * R; i += BLOCK) s_wh[i] = (unsigned short)(s_wh[i] + s_dstart[i & (R - 1)]);
     if (IN != IN_GEN) cp_async_wait_all();
     __syncthreads();
     // stage the tile in shared memory in locally sorted order
@@ -1191,7 +1184,7 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
         if (e < cnt) {
             const unsigned d = (keys[i] >> sh) & mk;
             const unsigned rk = (ranks[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
-            const unsigned pos = s_wh[w * R + d] + rk;
+            const unsigned pos = s_dstart[d] + s_wh[w * R + d] + rk;
             if (pos < cnt)
                 s_elem[pos] = pack_kv(keys[i], s_vin[e]);
             else
