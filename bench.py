@@ -569,12 +569,21 @@ def run_ours(args, rank, world, local):
             "all_kernels_gbs": tot_bytes / (tot_ms / 1e3) / 1e9,
             "all_kernels_frac": tot_bytes / (tot_ms / 1e3) / 1e9 / peak}
 
-    cpu = None
+    cpu = cpu_par = None
     if not args.no_cpu_baseline and world == 1:
         rate, dt, ntri, nr = cpu_oracle_rate(scene, 1)
         cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
                "sample": f"whole {args.workload} ({ntri} triangles, {nr} pairs), counting placement, "
                          f"single-threaded C, {dt:.1f} s"}
+        import oracle
+        threads = oracle.parallel_threads(0)
+        oracle.grid_parallel(scene.verts, scene.tris, scene.lam)   # warm (page-in, thread pool)
+        t0 = time.perf_counter()
+        _, _, npar = oracle.grid_parallel(scene.verts, scene.tris, scene.lam)
+        dtp = time.perf_counter() - t0
+        cpu_par = {"value": npar / dtp, "unit": METRIC, "cores": threads,
+                   "kind": "the oracle's steps under OpenMP, z-slab counting placement",
+                   "sample": f"whole {args.workload}, {dtp:.2f} s, grid equal to the oracle's"}
 
     extras = {}
     if not args.no_extras and world == 1:
@@ -606,7 +615,7 @@ def run_ours(args, rank, world, local):
                    "l2": l2_note,
                    "parallelism": f"replicas{world}"},
         "builds_per_s": world * args.steps / (ms_max / 1e3),
-        "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "cpu_baseline_parallel": cpu_par, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(),
     }
     out.update(extras)

@@ -91,6 +91,66 @@ def _bind(lib):
     return lib
 
 
+_PAR_SRC = os.path.join(_HERE, "cpu_parallel.c")
+_PAR_LIB = os.path.join(_BUILD_DIR, "libcpu_parallel.so")
+_par = None
+
+
+def build_parallel_library(force: bool = False) -> str:
+    """Compile the multi-core CPU baseline (cpu_parallel.c with the oracle's
+    own steps, OpenMP) into _build/libcpu_parallel.so (if stale)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_PAR_LIB)
+            and os.path.getmtime(_PAR_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_PAR_SRC))):
+        return _PAR_LIB
+    tmp = _PAR_LIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+                    "-o", tmp, _PAR_SRC, _SRC, "-lm"], check=True)
+    os.replace(tmp, _PAR_LIB)
+    return _PAR_LIB
+
+
+def _load_parallel():
+    global _par
+    with _lock:
+        if _par is None:
+            lib = ctypes.CDLL(build_parallel_library())
+            P, I64 = ctypes.c_void_p, ctypes.c_int64
+            lib.cp_threads.argtypes = [ctypes.c_int]
+            lib.cp_threads.restype = ctypes.c_int
+            lib.cp_build_grid.argtypes = [P, I64, P, I64, ctypes.c_float, P, I64, P, I64, P, P]
+            lib.cp_build_grid.restype = ctypes.c_int
+            _par = lib
+    return _par
+
+
+def parallel_threads(nthreads: int = 0) -> int:
+    """Threads the multi-core baseline uses (0: every host core)."""
+    return int(_load_parallel().cp_threads(int(nthreads)))
+
+
+def grid_parallel(verts, tris, lam: float, nthreads: int = 0):
+    """The multi-core CPU baseline (a benchmark reference point, not a pin):
+    the oracle's steps under OpenMP with an atomic counting placement and a
+    per-cell sort.  Returns (G, refs, NO), equal to build_grid's."""
+    lib = _load_parallel()
+    lib.cp_threads(int(nthreads))
+    v = _c(verts, np.float32, (-1, 3))
+    t = _c(tris, np.int32, (-1, 3))
+    nc = np.zeros(1, np.int64)
+    nr = np.zeros(1, np.int64)
+    G = np.zeros(1, np.int32)
+    rc = lib.cp_build_grid(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.c_float(lam), _p(G), 0, None, 0,
+                           _p(nc), _p(nr))
+    if rc not in (OK, EOVERFLOW):
+        _check(rc, "grid_parallel")
+    G = np.zeros(int(nc[0]) + 1, np.int32)
+    refs = np.zeros(max(int(nr[0]), 1), np.int32)
+    _check(lib.cp_build_grid(_p(v), v.shape[0], _p(t), t.shape[0], ctypes.c_float(lam), _p(G), G.shape[0],
+                             _p(refs), refs.shape[0], _p(nc), _p(nr)), "grid_parallel")
+    return G, refs[: int(nr[0])].copy(), int(nr[0])
+
+
 def use_library(path: str) -> None:
     """Points this module at another build of oracle.c (the mutation tests
     plant mistakes in copies of it to show the pins catch them)."""
