@@ -283,6 +283,20 @@ int grid_sort_pairs(grid_ctx *ctx, const int32_t *C, const int32_t *O, int64_t c
 int grid_extract_ranges(grid_ctx *ctx, const int32_t *C_sorted, int64_t count, int64_t ncells,
                         int32_t *cells);
 
+/* ---- failure detection ------------------------------------------------------ */
+
+/* Self-test of the kernels' bounded waits (not a step of the method).  Every
+ * decoupled look-back (pair count scan, radix-sort passes, culling
+ * compaction) polls a predecessor's status word at most 2^20 times with a
+ * back-off. If the word never arrives, the kernel records a timeout, stops
+ * waiting and finishes, and the call returns GRID_ETIMEOUT with the context
+ * still usable.  This runs the sort passes' look-back against a
+ * predecessor that never publishes, on the context's stream, and returns
+ * what a build would: GRID_ETIMEOUT (the expected answer), or GRID_OK /
+ * GRID_ECUDA if the wait did not behave.  *elapsed_ms (may be NULL) gets the
+ * wait's device time (about a second or less).  Synchronises. */
+int grid_selftest_wait_timeout(grid_ctx *ctx, double *elapsed_ms);
+
 /* ---- per-request vertex jitter ------------------------------------------- */
 
 /* Not a step of the method: the perturbation the serving loop applies to a

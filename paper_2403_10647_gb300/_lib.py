@@ -104,6 +104,7 @@ SIGNATURES = {
     "grid_sort_pairs": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p]),
     "grid_extract_ranges": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_void_p]),
     "grid_extract_ranges_noalloc": (c_int32, [c_void_p, c_int64, c_int64, c_void_p, c_void_p]),
+    "grid_selftest_wait_timeout": (c_int32, [c_void_p, P(ctypes.c_double)]),
     "grid_jitter": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_float, ctypes.c_uint64]),
     "grid_serve_create": (c_int32, [ctypes.c_int, P(GridServeOpts), P(c_void_p)]),
     "grid_serve_destroy": (None, [c_void_p]),

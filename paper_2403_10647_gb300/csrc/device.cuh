@@ -27,7 +27,7 @@ struct Ctl {
     unsigned lo_inv[3];         // atomicMax of ~ordered(min coordinate) per axis
     unsigned hi_ord[3];         // atomicMax of ordered(max coordinate) per axis
     unsigned err;               // ERR_* bits
-    unsigned hist_done;         // blocks of the digit-histogram kernel that finished
+    unsigned spare;             // unused (keeps the layout)
     unsigned long long nrefs;   // NO, written by the last count/scan tile
     unsigned tickets[8];        // tile tickets: [0] count/scan, [7] culling emit
     unsigned long long nkept;   // pairs the culling emit kept, written by its last tile

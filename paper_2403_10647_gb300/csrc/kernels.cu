@@ -821,6 +821,15 @@ __device__ __forceinline__ unsigned group_lookback(const unsigned *col, unsigned
     return excl;
 }
 
+// Failure-detection self-test: the sort's look-back run as group 1 of a
+// column whose group-0 word nothing ever publishes.  The wait gives up after
+// SPIN_LIMIT polls and records ERR_TIMEOUT, as a real look-back would if a
+// predecessor never arrived.
+__global__ void wait_selftest_kernel(const unsigned *col, Ctl *ctl, unsigned *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = group_lookback(col, 1u, 1u, ctl);
+}
+
 template <int BLOCK, int ITEMS, int RBITS, int SRC>
 __global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
 {
@@ -829,15 +838,13 @@ __global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
     extern __shared__ __align__(16) unsigned smem[];
     unsigned *s_cnt = smem;                          // [R] this tile's digit counts
     unsigned *s_run = s_cnt + R;                     // [R] counts of the group's tiles so far
-    unsigned *s_hist = s_run + R;                    // [MAX_PASSES][R] later passes' digits (with_hist)
-    unsigned *s_mark = s_hist + MAX_PASSES * R;      // [padded T] object marks (generated pairs)
+    unsigned *s_mark = s_run + R;                    // [padded T] object marks (generated pairs)
     __shared__ unsigned s_tmp[BLOCK / 32];
-    __shared__ unsigned s_last;
     const int tid = threadIdx.x;
     const unsigned g = blockIdx.x;
     const unsigned t0 = g * GROUP_TILES, t1 = min(t0 + GROUP_TILES, a.ntiles);
-    const unsigned sh = a.shift[0], mk = (1u << a.bits[0]) - 1u;
-    for (int i = tid; i < (2 + MAX_PASSES) * R; i += BLOCK) smem[i] = 0u;
+    const unsigned sh = a.shift, mk = (1u << a.bits) - 1u;
+    for (int i = tid; i < 2 * R; i += BLOCK) smem[i] = 0u;
     __syncthreads();
 
     for (unsigned t = t0; t < t1; ++t) {
@@ -891,26 +898,6 @@ __global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i)
             if ((unsigned)i < nv) atomicAdd(&s_cnt[(keys[i] >> sh) & mk], 1u);
-        if (a.with_hist) {
-            // later passes' digits repeat along a thread's run of consecutive
-            // pairs: one shared atomic per run (predicated, no branches)
-#pragma unroll
-            for (int p = 1; p < MAX_PASSES; ++p) {
-                if (p >= a.npasses) break;
-                const unsigned shp = a.shift[p], mkp = (1u << a.bits[p]) - 1u;
-                unsigned prev = (keys[0] >> shp) & mkp, run = nv ? 1u : 0u;
-#pragma unroll
-                for (int i = 1; i < ITEMS; ++i) {
-                    const unsigned d = (keys[i] >> shp) & mkp;
-                    const bool more = (unsigned)i < nv;
-                    const bool flush = more && d != prev;
-                    if (flush) atomicAdd(&s_hist[p * R + prev], run);
-                    run = flush ? 1u : run + (more ? 1u : 0u);
-                    prev = flush ? d : prev;
-                }
-                if (run) atomicAdd(&s_hist[p * R + prev], run);
-            }
-        }
         __syncthreads();
         for (int d = tid; d < R; d += BLOCK) {
             a.intra[(size_t)t * R + d] = (unsigned short)s_run[d];
@@ -933,39 +920,22 @@ __global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
             st_relaxed_u32(col + (size_t)g * R, LB_PREFIX | (excl + tot));
         }
         a.gpref[(size_t)g * R + d] = excl;
+        s_cnt[d] = excl + tot;
     }
-    if (!a.with_hist) return;
-
-    // digit totals of every pass -> exclusive digit starts (last block)
+    // the last group's inclusive prefixes are the pass's digit totals: its
+    // block turns them into the digit starts the downsweep adds
+    if (g != gridDim.x - 1) return;
     __syncthreads();
-    for (int i = tid; i < a.npasses * R; i += BLOCK) {
-        const unsigned v = i < R ? s_run[i] : s_hist[i];
-        if (v) atomicAdd(&a.hist[(i / R) * MAX_RADIX + (i % R)], v);
+    const int nd = 1 << a.bits;
+    unsigned carry = 0;
+    for (int c0 = 0; c0 < nd; c0 += BLOCK) {
+        const int d = c0 + tid;
+        const unsigned v = d < nd ? s_cnt[d] : 0u;
+        unsigned tot;
+        const unsigned ex = block_excl_sum<BLOCK>(v, s_tmp, &tot);
+        if (d < nd) a.dbase[d] = carry + ex;
+        carry += tot;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&a.ctl->hist_done, 1u) == gridDim.x - 1u);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-#pragma unroll
-    for (int p = 0; p < MAX_PASSES; ++p) {
-        if (p >= a.npasses) break;
-        const int nd = 1 << a.bits[p];
-        unsigned carry = 0;
-        for (int c0 = 0; c0 < nd; c0 += BLOCK) {
-            const int d = c0 + tid;
-            const unsigned v = d < nd ? __ldcg(&a.hist[p * MAX_RADIX + d]) : 0u;
-            unsigned tot;
-            const unsigned ex = block_excl_sum<BLOCK>(v, s_tmp, &tot);
-            if (d < nd) {
-                a.dbase[p * MAX_RADIX + d] = carry + ex;
-                a.hist[p * MAX_RADIX + d] = 0u;   // leave the histogram zeroed for the next use
-            }
-            carry += tot;
-        }
-    }
-    if (tid == 0) a.ctl->hist_done = 0u;
 }
 
 // Shared-memory index for 64-bit elements: one pad element per 16, so blocked
@@ -1488,6 +1458,12 @@ cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_wait_selftest(const unsigned *col, Ctl *ctl, unsigned *out, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 32, 0, s>>>(col, ctl, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cull_emit(const CullArgs &a, cudaStream_t s)
 {
     if (a.count == 0) return cudaSuccess;
@@ -1505,7 +1481,7 @@ static cudaError_t launch_up_t(const UpArgs &a, cudaStream_t s)
 {
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
     auto k = upsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, SRC>;
-    const size_t smem = sizeof(unsigned) * ((2 + MAX_PASSES) * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
+    const size_t smem = sizeof(unsigned) * (2 * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
     static std::atomic<unsigned long long> configured{0};
     if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
     const unsigned groups = (a.ntiles + GROUP_TILES - 1) / GROUP_TILES;

@@ -99,9 +99,8 @@ struct CullArgs {
 };
 
 // Upsweep of one radix-sort pass: digit counts per tile, offsets of each
-// tile inside its group of GROUP_TILES tiles, offsets of each group.  With
-// with_hist it also counts the digits of every pass and writes the digit
-// starts (dbase) of all passes.
+// tile inside its group of GROUP_TILES tiles, offsets of each group, and,
+// from the last group's inclusive prefixes, the pass's digit starts.
 struct UpArgs {
     const unsigned *keys_in;        // SRC_MEM
     const ObjRec *recs;             // SRC_GEN
@@ -112,16 +111,12 @@ struct UpArgs {
     unsigned *gen_vals;             //   (object order, [count] each) for the first downsweep
     unsigned count;
     unsigned ntiles;
-    int npasses;                    // with_hist: passes counted; shift[0]/bits[0] = this pass
-    int shift[MAX_PASSES];
-    int bits[MAX_PASSES];
-    int with_hist;
+    int shift, bits;                // this pass's digit
     unsigned short *intra;          // [ntiles][2^RBITS] out: tile offsets inside its group
                                     // (< GROUP_TILES * PAIR_TILE <= 65536)
     unsigned *gpref;                // [ngroups][2^RBITS] out: group offsets
     unsigned *status;               // [ngroups][2^RBITS] look-back words, zero on entry
-    unsigned *hist;                 // [MAX_PASSES][MAX_RADIX], zero on entry and exit (with_hist)
-    unsigned *dbase;                // [MAX_PASSES][MAX_RADIX] out (with_hist)
+    unsigned *dbase;                // [2^bits] out: the pass's digit starts (written by the last group)
     Ctl *ctl;
 };
 
@@ -185,6 +180,8 @@ cudaError_t launch_tile_search(const ObjRec *recs, long long n, unsigned tile, u
                                unsigned *tile_obj, cudaStream_t s);
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s);
 cudaError_t launch_cull_emit(const CullArgs &a, cudaStream_t s);
+// Runs the look-back wait on col[0], which must be zero and stay zero.
+cudaError_t launch_wait_selftest(const unsigned *col, Ctl *ctl, unsigned *out, cudaStream_t s);
 // Pair-generation ablation (sorted_grid.cu): one thread per object writes its
 // pairs C[start ..], O[start ..] (single mesh).
 cudaError_t launch_make_pairs_per_object(const ObjRec *recs, long long n, unsigned res_x, unsigned res_y,

@@ -72,7 +72,6 @@ struct grid_ctx {
 
     Ctl *d_ctl = nullptr;        // device control block
     Ctl *h_ctl = nullptr;        // pinned host mirror
-    unsigned *d_hist = nullptr;  // [MAX_PASSES][MAX_RADIX], kept zero between uses
     unsigned *d_dbase = nullptr; // [MAX_PASSES][MAX_RADIX]
 
     Scratch recs, k2status, tile_obj, keys_sorted, keys[1], vals[1], intra, gpref, gstatus, splits;
@@ -360,18 +359,12 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         u.gen_vals = first ? gv : nullptr;
         u.count = count;
         u.ntiles = ntiles;
-        u.with_hist = first ? 1 : 0;
-        u.npasses = first ? sc.passes : 1;
-        for (int q = 0; q < gg::MAX_PASSES; ++q) {
-            const int pq = first ? q : p;   // with_hist: every pass's digit; else this pass's
-            u.shift[q] = sc.shift[pq < gg::MAX_PASSES ? pq : 0];
-            u.bits[q] = sc.bits[pq < gg::MAX_PASSES ? pq : 0];
-        }
+        u.shift = sc.shift[p];
+        u.bits = sc.bits[p];
         u.intra = (unsigned short *)c->intra.ptr;
         u.gpref = (unsigned *)c->gpref.ptr;
         u.status = (unsigned *)c->gstatus.ptr;
-        u.hist = c->d_hist;
-        u.dbase = c->d_dbase;
+        u.dbase = c->d_dbase + p * gg::MAX_RADIX;
         u.ctl = c->d_ctl;
         const bool gen_up = first && gen;
         const bool gen_down = gen_up && !store;
@@ -731,13 +724,12 @@ int grid_ctx_create(int device, const grid_opts *opts, grid_ctx **out)
         if ((rc = cuda_err(cudaMemPoolCreate(&c->pool, &props)))) break;
         uint64_t thr = UINT64_MAX;
         if ((rc = cuda_err(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr)))) break;
-        const size_t small = sizeof(Ctl) + 2 * sizeof(unsigned) * gg::MAX_PASSES * gg::MAX_RADIX;
+        const size_t small = sizeof(Ctl) + sizeof(unsigned) * gg::MAX_PASSES * gg::MAX_RADIX;
         void *p = nullptr;
         if ((rc = cuda_err(cudaMalloc(&p, small)))) break;
         if ((rc = cuda_err(cudaMemset(p, 0, small)))) break;
         c->d_ctl = (Ctl *)p;
-        c->d_hist = (unsigned *)((char *)p + sizeof(Ctl));
-        c->d_dbase = c->d_hist + gg::MAX_PASSES * gg::MAX_RADIX;
+        c->d_dbase = (unsigned *)((char *)p + sizeof(Ctl));
         if ((rc = cuda_err(cudaMallocHost(&p, sizeof(Ctl))))) break;
         c->h_ctl = (Ctl *)p;
         std::memset(c->h_ctl, 0, sizeof(Ctl));
@@ -1117,6 +1109,35 @@ void grid_buf_free(grid_ctx *c, grid_buf *b)
     DeviceGuard g(c->device);
     pool_free(c, b->ptr, b->bytes);
     *b = grid_buf{nullptr, 0, 0};
+}
+
+int grid_selftest_wait_timeout(grid_ctx *c, double *elapsed_ms)
+{
+    if (!c) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    GG_TRY(reset_ctl(c));
+    GG_TRY(ensure(c, c->splits, 16));   // word 0: the column nothing publishes, word 1: the result
+    unsigned *w = (unsigned *)c->splits.ptr;
+    GG_CUDA(cudaMemsetAsync(w, 0, 16, c->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return GRID_ECUDA;
+    }
+    cudaEventRecord(e0, c->stream);
+    int rc = cuda_err(gg::launch_wait_selftest(w, c->d_ctl, w + 1, c->stream));
+    cudaEventRecord(e1, c->stream);
+    if (rc == GRID_OK) rc = read_ctl(c);
+    if (rc == GRID_OK) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (elapsed_ms) *elapsed_ms = ms;
+        rc = ctl_error(c->h_ctl->err);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int grid_jitter(grid_ctx *c, const float *verts, float *out, int64_t nverts, float sigma, uint64_t seed)

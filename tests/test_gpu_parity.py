@@ -389,3 +389,21 @@ def test_batched_64_meshes_match_plain(ctx):
         if k in check_oracle:
             assert_grid_equal(g, oracle.build_grid(s.verts, s.tris, s.lam, method="counting"), f"mesh {k}")
         del p
+
+
+# ---- failure detection ------------------------------------------------------------------
+
+def test_bounded_wait_times_out_and_context_survives(ctx):
+    """The sort's look-back, waiting on a predecessor that never publishes,
+    gives up after its poll limit: the call returns GRID_ETIMEOUT within
+    seconds, and the same context then builds a grid correctly."""
+    import ctypes
+    from paper_2403_10647_gb300 import _lib
+    lib = _lib.load()
+    ms = ctypes.c_double()
+    rc = lib.grid_selftest_wait_timeout(ctx._h, ctypes.byref(ms))
+    assert rc == _lib.GRID_ETIMEOUT, lib.grid_strerror(rc)
+    assert 0.0 < ms.value < 10_000.0, ms.value
+    s = scenes.uniform_soup(5_000, seed=99)
+    g, o = build_both(ctx, s)
+    assert_grid_equal(g, o, "after a timed-out wait")
