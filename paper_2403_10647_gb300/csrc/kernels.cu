@@ -1221,6 +1221,7 @@ template <int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
 {
     constexpr int D = BLOCK * ITEMS;
+    static_assert((D & (D - 1)) == 0, "the lower-bound steps halve from D");
     __shared__ unsigned s_keys[D];
     __shared__ unsigned s_g[D];
     const int tid = threadIdx.x;
@@ -1259,31 +1260,17 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
         }
     }
     __syncthreads();
-    // each thread merges ITEMS consecutive items of the block's range: one
-    // merge-path search for where its diagonal crosses the keys, then a
-    // sequential walk (a cell takes the count of keys taken before it)
-    const unsigned dt = min((unsigned)(tid * ITEMS), nd);
-    unsigned lo = dt > nc ? dt - nc : 0u, hi = min(dt, na);
-    while (lo < hi) {
-        const unsigned mid = (lo + hi) >> 1;
-        // key mid precedes cell c0 + (dt - mid - 1)?
-        if (s_keys[mid] < c0 + (dt - mid - 1u))
-            lo = mid + 1u;
-        else
-            hi = mid;
-    }
-    unsigned i = lo, c = c0 + (dt - lo);
-    const unsigned end = min(dt + (unsigned)ITEMS, nd);
+    // each cell of the block's range: a branch-free lower bound over the
+    // block's keys (every lane takes the same fixed number of steps)
+    for (unsigned k = tid; k < nc; k += BLOCK) {
+        const unsigned c = c0 + k;
+        unsigned pos = 0;
 #pragma unroll
-    for (int step = 0; step < ITEMS; ++step) {
-        if (i + (c - c0) < end) {
-            if (i < na && s_keys[i] < c) {
-                ++i;
-            } else {
-                s_g[c - c0] = (unsigned)i0 + i;
-                ++c;
-            }
+        for (unsigned step = (unsigned)D; step >= 1u; step >>= 1) {   // D, a power of two, bounds na
+            const unsigned q = pos + step;
+            pos = (q <= na && s_keys[q - 1u] < c) ? q : pos;
         }
+        s_g[k] = (unsigned)i0 + pos;
     }
     __syncthreads();
     for (unsigned k = tid; k < nc; k += BLOCK) a.G[(unsigned long long)c0 + k] = s_g[k];
