@@ -355,7 +355,8 @@ typedef struct {
     int64_t reserved_bytes;     /* admission reservations now */
     int64_t peak_reserved_bytes;
     int64_t budget_bytes;
-    double p50_us, p99_us, mean_us, max_us;   /* latency, submit -> result ready */
+    double p50_us, p99_us, mean_us, max_us;   /* latency, submit -> result ready; the
+                                                 percentiles to 1% (log-bucketed counts) */
     double p50_service_us;      /* build time of a request's batch, median */
     double builds_per_s;        /* completed / (last completion - first submission) */
     double elapsed_s;           /* that interval */
@@ -374,7 +375,9 @@ int grid_serve_register(grid_server *srv, const float *verts, int64_t nverts, co
                         int64_t n, float lambda, int32_t *mesh_id);
 /* Queues a rebuild of mesh_id with jitter sigma (>= 0; 0 = the registered
  * vertices) and seed; *ticket identifies it.  GRID_EAGAIN when admission
- * refuses (nothing queued), GRID_EINVAL for an unknown mesh or bad sigma. */
+ * refuses for now (nothing queued), GRID_ELIMIT when the request's estimate
+ * alone exceeds the budget (it can never be admitted), GRID_EINVAL for an
+ * unknown mesh or bad sigma. */
 int grid_serve_submit(grid_server *srv, int32_t mesh_id, float sigma, uint64_t seed, uint64_t *ticket);
 /* If the request has finished: GRID_OK with views of its result (device
  * pointers owned by the server, valid until grid_serve_release; never pass

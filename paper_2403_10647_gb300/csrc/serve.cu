@@ -91,15 +91,46 @@ struct Worker {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-double percentile(std::vector<double> v, double q)
-{
-    if (v.empty()) return 0.0;
-    std::sort(v.begin(), v.end());
-    // nearest rank
-    size_t k = (size_t)std::ceil(q * (double)v.size());
-    k = std::min(std::max<size_t>(k, 1), v.size());
-    return v[k - 1];
-}
+// Latency statistics in bounded memory: counts in geometric buckets of 1%
+// width from 1 us up (values below 1 us share bucket 0), plus the exact
+// count, sum and maximum.  A percentile is reported as its bucket's upper
+// edge, within 1% above the exact nearest-rank value.
+struct LatencyHist {
+    static constexpr int NB = 2400;          // 1.01^2400 us, about 2.2e10 us: beyond any wait
+    std::vector<uint64_t> counts = std::vector<uint64_t>(NB, 0);
+    uint64_t n = 0;
+    double sum = 0.0, max = 0.0;
+    static int bucket(double us)
+    {
+        if (!(us > 1.0)) return 0;
+        const int b = 1 + (int)(std::log(us) / std::log(1.01));
+        return b < NB ? b : NB - 1;
+    }
+    void add(double us)
+    {
+        counts[bucket(us)] += 1;
+        n += 1;
+        sum += us;
+        max = std::max(max, us);
+    }
+    double percentile(double q) const
+    {
+        if (n == 0) return 0.0;
+        uint64_t k = (uint64_t)std::ceil(q * (double)n), acc = 0;   // nearest rank
+        if (k < 1) k = 1;
+        for (int b = 0; b < NB; ++b) {
+            acc += counts[b];
+            if (acc >= k) return std::min(b == 0 ? 1.0 : std::pow(1.01, (double)b), max);
+        }
+        return max;
+    }
+    void clear()
+    {
+        std::fill(counts.begin(), counts.end(), 0);
+        n = 0;
+        sum = max = 0.0;
+    }
+};
 
 }  // namespace
 
@@ -192,7 +223,7 @@ struct grid_server {
 
     // statistics since the last reset
     int64_t submitted = 0, completed = 0, failed = 0, refused = 0, batches = 0, batched_requests = 0;
-    std::vector<double> lat_us, service_us;
+    LatencyHist lat_us, service_us;
     bool have_first = false;
     Clock::time_point t_first{}, t_last{};
 };
@@ -383,8 +414,8 @@ void worker_main(grid_server *S, Worker *w)
                 r->state = Q_DONE;
                 S->completed += 1;
                 if (r->rc != GRID_OK) S->failed += 1;
-                S->lat_us.push_back(std::chrono::duration<double, std::micro>(t1 - r->t_submit).count());
-                S->service_us.push_back(service);
+                S->lat_us.add(std::chrono::duration<double, std::micro>(t1 - r->t_submit).count());
+                S->service_us.add(service);
             }
             S->batches += 1;
             if (rs.size() > 1) S->batched_requests += (int64_t)rs.size();
@@ -570,6 +601,7 @@ int grid_serve_submit(grid_server *S, int32_t mesh_id, float sigma, uint64_t see
         std::lock_guard<std::mutex> lk(S->mu);
         if (mesh_id < 0 || (size_t)mesh_id >= S->meshes.size()) return GRID_EINVAL;
         const int64_t est = S->meshes[mesh_id].est_bytes;
+        if (est > S->budget) return GRID_ELIMIT;   // would not fit even with nothing else admitted
         if (S->reserved + est > S->budget) {
             S->refused += 1;
             return GRID_EAGAIN;
@@ -656,7 +688,6 @@ int grid_serve_get_stats(grid_server *S, grid_serve_stats *o, int reset)
 {
     if (!S || !o) return GRID_EINVAL;
     std::memset(o, 0, sizeof(*o));
-    std::vector<double> lat, svc;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         o->submitted = S->submitted;
@@ -673,8 +704,13 @@ int grid_serve_get_stats(grid_server *S, grid_serve_stats *o, int reset)
             o->elapsed_s = std::chrono::duration<double>(S->t_last - S->t_first).count();
             o->builds_per_s = (double)S->completed / o->elapsed_s;
         }
-        lat = S->lat_us;
-        svc = S->service_us;
+        if (S->lat_us.n) {
+            o->mean_us = S->lat_us.sum / (double)S->lat_us.n;
+            o->max_us = S->lat_us.max;
+            o->p50_us = S->lat_us.percentile(0.50);
+            o->p99_us = S->lat_us.percentile(0.99);
+            o->p50_service_us = S->service_us.percentile(0.50);
+        }
         if (reset) {
             S->submitted = S->completed = S->failed = S->refused = S->batches = S->batched_requests = 0;
             S->lat_us.clear();
@@ -682,18 +718,6 @@ int grid_serve_get_stats(grid_server *S, grid_serve_stats *o, int reset)
             S->have_first = false;
             S->peak_reserved = S->reserved;
         }
-    }
-    if (!lat.empty()) {
-        double sum = 0.0, mx = 0.0;
-        for (double v : lat) {
-            sum += v;
-            mx = std::max(mx, v);
-        }
-        o->mean_us = sum / (double)lat.size();
-        o->max_us = mx;
-        o->p50_us = percentile(lat, 0.50);
-        o->p99_us = percentile(lat, 0.99);
-        o->p50_service_us = percentile(svc, 0.50);
     }
     return GRID_OK;
 }

@@ -278,3 +278,36 @@ def test_empty_mesh_is_served(ctx):
         r.release()
     finally:
         srv.close()
+
+
+def test_request_larger_than_the_budget_is_rejected_for_good(ctx, pool):
+    """A request whose estimate alone exceeds the budget can never be
+    admitted: GRID_ELIMIT, not the retry-later GRID_EAGAIN."""
+    import paper_2403_10647_gb300 as pg
+    from paper_2403_10647_gb300 import _lib
+    srv = pg.Server(0, nworkers=1, hbm_budget=1 << 20)   # below any request's estimate
+    try:
+        mid = srv.register(pool[0].verts, pool[0].tris, pool[0].lam)
+        with pytest.raises(pg.GridError) as e:
+            srv.submit(mid, 0.01, 1)
+        assert e.value.code == _lib.GRID_ELIMIT
+        st = srv.stats()
+        assert st["submitted"] == 0 and st["reserved_bytes"] == 0
+    finally:
+        srv.close()
+
+
+def test_latency_statistics(ctx, pool):
+    import paper_2403_10647_gb300 as pg
+    srv = pg.Server(0, nworkers=2, max_batch=4)
+    try:
+        ids = [srv.register(s.verts, s.tris, s.lam) for s in pool[:3]]
+        for k in range(30):
+            srv.wait(srv.submit(ids[k % 3], 0.01, k), timeout=120).release()
+        st = srv.stats(reset=True)
+        assert st["completed"] == 30
+        assert 0 < st["p50_us"] <= st["p99_us"] <= st["max_us"] * 1.0 + 1e-9
+        assert st["mean_us"] <= st["max_us"] and st["p50_service_us"] > 0
+        assert srv.stats()["completed"] == 0   # reset cleared the counters
+    finally:
+        srv.close()
