@@ -364,7 +364,8 @@ def bench_cull(scene, reps: int = 5):
     return out
 
 
-def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 4, max_batch: int = 32):
+def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 2, max_batch: int = 32, batch_pairs: int = 0,
+                radix_bits: int = 8):
     """The rebuild-serving loop: a pool of registered meshes, requests with
     per-request jitter (sigma 0.01).  (1) open loop: Poisson arrivals at
     `rate` for `seconds`, latency percentiles; (2) saturated: the first 1000
@@ -378,7 +379,7 @@ def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 4, max_batch: 
     pool = scenes.serving_pool()
     arr, mesh, seeds = scenes.poisson_requests(rate, seconds, len(pool))
     sigma = 0.01
-    srv = pg.Server(0, nworkers=nworkers, max_batch=max_batch)
+    srv = pg.Server(0, nworkers=nworkers, max_batch=max_batch, batch_pairs=batch_pairs, radix_bits=radix_bits)
     try:
         ids = [srv.register(s.verts, s.tris, s.lam) for s in pool]
         # warm every worker and mesh once
@@ -462,7 +463,7 @@ def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 4, max_batch: 
     finally:
         srv.close()
     return {"pool_meshes": len(pool), "pool_tris": [int(min(s.n for s in pool)), int(max(s.n for s in pool))],
-            "sigma": sigma, "workers": nworkers, "max_batch": max_batch,
+            "sigma": sigma, "workers": nworkers, "max_batch": max_batch, "batch_pairs": batch_pairs or (1 << 24),
             "open_loop": open_loop, "saturated": saturated}
 
 
@@ -626,7 +627,7 @@ def run_ours(args, rank, world, local):
     if not args.no_extras and world == 1:
         extras["batched"] = bench_batched(ctx, 1.0)
         extras["batched_small"] = bench_batched(ctx, 0.01, reps=20)
-        extras["serve"] = bench_serve(ctx, args.serve_seconds, args.serve_rate)
+        extras["serve"] = bench_serve(ctx, args.serve_seconds, args.serve_rate, radix_bits=args.radix_bits)
         extras["pair_gen_ablation"] = {args.workload: bench_pair_gen(scene)}
         extras["culling"] = {args.workload: bench_cull(scene)}
         if args.workload != "nonhomogeneous_1e6":

@@ -334,10 +334,11 @@ int grid_jitter(grid_ctx *ctx, const float *verts, float *out, int64_t nverts, f
 typedef struct grid_server grid_server;
 
 typedef struct {
-    int32_t nworkers;     /* worker threads / streams; 0 -> 4 */
+    int32_t nworkers;     /* worker threads / streams; 0 -> 2 */
     int32_t max_batch;    /* requests per batched build; 0 -> 32 */
     int64_t batch_pairs;  /* cap on a batch's estimated pairs (a larger single request runs alone);
-                             0 -> 2^27 */
+                             0 -> 2^24: batching pays for small meshes (fewer launches and
+                             synchronisations), while a batch of large ones sorts wider keys */
     int64_t hbm_budget;   /* bytes that admitted requests may reserve; 0 -> 3/4 of the device's free
                              memory when the server is created */
     int32_t radix_bits;   /* as grid_opts.radix_bits; 0 -> default */

@@ -463,9 +463,9 @@ int grid_serve_create(int device, const grid_serve_opts *opts, grid_server **out
     if (o.nworkers < 0 || o.nworkers > 64 || o.max_batch < 0 || o.max_batch > 4096 || o.batch_pairs < 0 ||
         o.hbm_budget < 0)
         return GRID_EINVAL;
-    if (o.nworkers == 0) o.nworkers = 4;
+    if (o.nworkers == 0) o.nworkers = 2;
     if (o.max_batch == 0) o.max_batch = 32;
-    if (o.batch_pairs == 0) o.batch_pairs = 1ll << 27;
+    if (o.batch_pairs == 0) o.batch_pairs = 1ll << 24;
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(device);
