@@ -154,9 +154,17 @@ def peaks():
 
 
 def kernels_digest() -> str:
+    """First 16 hex digits of the sha256 of csrc/kernels.cu's code with its
+    comments and whitespace removed: a comment edit keeps the committed
+    profiles valid, any code change does not."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2403_10647_gb300", "csrc", "kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    import re
+    with open(os.path.join(ROOT, "paper_2403_10647_gb300", "csrc", "kernels.cu")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = re.sub(r"\s+", "", src)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def sort_passes(key_bits: int, radix_bits: int):

@@ -12,13 +12,13 @@
 //                        + MakeCellIds (GlobalCoords): the object-order lists.
 //   upsweep_kernel       per-tile digit counts of one RadixSort pass, prefixed
 //                        across groups of tiles by a decoupled look-back; the
-//                        first pass generates its pairs (the emit steps above)
-//                        instead of reading them and also histograms every
-//                        later pass.
+//                        last group turns its prefixes into the pass's digit
+//                        starts.  The first pass generates its pairs (the emit
+//                        steps above) instead of reading them and stores them
+//                        once for its downsweep.
 //   downsweep_kernel     one stable LSD radix-sort pass (RadixSort of Algorithm
 //                        1): warp multisplit ranking, shared-memory staged,
-//                        coalesced scatter.  The first pass again generates its
-//                        pairs, so (C, O) in object order never touch HBM.
+//                        coalesced scatter.
 //   extract_kernel       RunLengthEncode + NonEmptyCells + ExclusiveSum fused as
 //                        a merge path of the sorted keys against the cell ids.
 //   bounds_batched_kernel, localize_kernel
@@ -771,9 +771,10 @@ __global__ void __launch_bounds__(BLOCK) cull_emit_kernel(CullArgs a)
 // order and writes each tile's digit offsets inside the group, then a
 // decoupled look-back across groups yields each group's offsets.  Groups
 // start GROUP_TILES times less often than tiles, so look-back chains stay
-// short at GB300's tile rate.  The first pass's upsweep generates the pairs
-// (no pair array exists yet) and also counts every later pass's digits, so
-// all digit totals are known before any scatter.
+// short at GB300's tile rate.  The last group's inclusive prefixes are the
+// pass's digit totals; its block scans them into the digit starts.  The
+// first pass's upsweep generates the pairs (no pair array exists yet) and
+// stores them for the first downsweep.
 //
 // Downsweep of pass p: every tile independently ranks its elements stably
 // by digit and scatters them to dbase[d] + group offset + tile offset +
