@@ -15,7 +15,7 @@ import dataclasses
 from . import _lib
 from ._lib import GridError, GridInfo, GridBuf, GridOpts, GridServeOpts, GridServeStats, check
 
-__all__ = ["Context", "Server", "Info", "Grid", "plan", "GridError"]
+__all__ = ["Context", "Server", "Info", "Grid", "BatchedGrids", "plan", "GridError"]
 
 
 @dataclasses.dataclass
@@ -47,6 +47,40 @@ class Grid:
     cells: "object"   # torch int32 [ncells + 1], CUDA
     refs: "object"    # torch int32 [nrefs], CUDA
     info: Info
+
+
+class BatchedGrids:
+    """The grids of a batched build: len(), indexing and iteration give one
+    Grid per mesh.  `cells` and `refs` are the two library buffers holding
+    every mesh's arrays back to back; `cells_offsets` / `refs_offsets` say
+    where each mesh's arrays start."""
+
+    def __init__(self, cells, refs, infos, cells_offsets, refs_offsets):
+        self.cells, self.refs = cells, refs
+        self._infos = infos
+        self.cells_offsets = [int(x) for x in cells_offsets]
+        self.refs_offsets = [int(x) for x in refs_offsets]
+        self._grids = [None] * len(self.cells_offsets)
+
+    def __len__(self):
+        return len(self._grids)
+
+    def __getitem__(self, m):
+        if isinstance(m, slice):
+            return [self[k] for k in range(*m.indices(len(self)))]
+        m = int(m)
+        if m < 0:
+            m += len(self)
+        if not 0 <= m < len(self):
+            raise IndexError("mesh index out of range")
+        if self._grids[m] is None:
+            info = Info.from_c(self._infos[m])
+            c0, r0 = self.cells_offsets[m], self.refs_offsets[m]
+            self._grids[m] = Grid(self.cells[c0:c0 + info.ncells + 1], self.refs[r0:r0 + info.nrefs], info)
+        return self._grids[m]
+
+    def __iter__(self):
+        return (self[m] for m in range(len(self)))
 
 
 def plan(lo, hi, n: int, lam: float) -> Info:
@@ -119,7 +153,7 @@ class Context:
         if not (isinstance(t, torch.Tensor) and t.device == self.device and t.dtype == dtype
                 and t.is_contiguous()):
             t = torch.as_tensor(t).to(device=self.device, dtype=dtype).contiguous()
-        if cols is not None:
+        if cols is not None and not (t.dim() == 2 and t.shape[1] == cols):
             t = t.reshape(-1, cols)
         return t
 
@@ -179,10 +213,11 @@ class Context:
                                    ctypes.byref(cb), ctypes.byref(rb), ctypes.byref(info)), "grid_build")
         return Grid(self._wrap(cb), self._wrap(rb), Info.from_c(info))
 
-    def build_batched(self, meshes) -> list:
+    def build_batched(self, meshes) -> "BatchedGrids":
         """BuildParallelGrid of every (verts, tris, lam) in `meshes` at once.
-        Returns one Grid per mesh whose cells / refs are views into two
-        library buffers (bit-identical to building each mesh alone)."""
+        Returns a sequence with one Grid per mesh whose cells / refs are views
+        into two library buffers (bit-identical to building each mesh
+        alone); a mesh's views are made when it is first accessed."""
         torch = self._torch
         keep = []
         arr = (_lib.GridMesh * len(meshes))()
@@ -200,13 +235,7 @@ class Context:
         self._bind_stream()
         check(self._lib.grid_build_batched(self._h, arr, nm, ctypes.byref(cb), ctypes.byref(rb), infos, coff, roff),
               "grid_build_batched")
-        cells, refs = self._wrap(cb), self._wrap(rb)
-        out = []
-        for m in range(nm):
-            info = Info.from_c(infos[m])
-            c0, r0 = int(coff[m]), int(roff[m])
-            out.append(Grid(cells[c0:c0 + info.ncells + 1], refs[r0:r0 + info.nrefs], info))
-        return out
+        return BatchedGrids(self._wrap(cb), self._wrap(rb), infos, coff, roff)
 
     def build_host(self, verts, tris, lam: float, cells_out=None, refs_out=None):
         """The same build from/to host memory (numpy arrays or CPU tensors,

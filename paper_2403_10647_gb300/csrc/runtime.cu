@@ -78,6 +78,9 @@ struct grid_ctx {
     Scratch in_verts, in_tris, out_cells, out_refs;  // host-buffer builds
     Scratch b_desc, b_base, b_state, b_pairbase, b_cellsoff, b_G;   // batched builds
     Scratch pairs_C, pairs_O;    // object-order pairs of the unfused pair_gen modes and of culling
+    void *h_stage = nullptr;     // pinned host tables of batched builds (grow-only)
+    size_t h_stage_bytes = 0;
+    bool stage_busy = false;     // a copy from h_stage may still be in flight
     Scratch cstatus;             // culling emit look-back words
     std::atomic<int64_t> in_use{0};
 
@@ -150,6 +153,29 @@ void release(grid_ctx *c, Scratch &s)
     pool_free(c, s.ptr, s.bytes);
     s.ptr = nullptr;
     s.bytes = 0;
+}
+
+// Pinned host staging of at least `bytes` for a batched build's tables, so
+// their copies are asynchronous.  If an earlier call left copies from it in
+// flight (it returned before its final synchronisation), wait for them first.
+int host_stage(grid_ctx *c, size_t bytes, char **out)
+{
+    if (c->stage_busy) {
+        GG_CUDA(cudaStreamSynchronize(c->stream));
+        c->stage_busy = false;
+    }
+    if (c->h_stage_bytes < bytes) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        const size_t want = (bytes + bytes / 2 + 4095) & ~size_t(4095);
+        void *p = nullptr;
+        GG_CUDA(cudaMallocHost(&p, want));
+        c->h_stage = p;
+        c->h_stage_bytes = want;
+    }
+    *out = (char *)c->h_stage;
+    return GRID_OK;
 }
 
 cudaEvent_t take_event(grid_ctx *c)
@@ -759,6 +785,7 @@ void grid_ctx_destroy(grid_ctx *c)
         c->free_events.clear();
         if (c->d_ctl) cudaFree(c->d_ctl);
         if (c->h_ctl) cudaFreeHost(c->h_ctl);
+        if (c->h_stage) cudaFreeHost(c->h_stage);
         if (c->pool) cudaMemPoolDestroy(c->pool);
         if (c->own) cudaStreamDestroy(c->own);
     }
@@ -936,7 +963,20 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
     *out_refs = grid_buf{nullptr, 0, 0};
     DeviceGuard g(c->device);
     const int nm = nmeshes;
-    std::vector<long long> obj_base(nm + 1, 0);
+    // the batch's host tables in pinned memory: descriptors, object bases,
+    // bounds state, cell offsets, pair bases (64-byte aligned each)
+    auto al = [](size_t b) { return (b + 63) & ~size_t(63); };
+    const size_t sz_desc = al(sizeof(gg::MeshDesc) * nm), sz_base = al(sizeof(long long) * (nm + 1)),
+                 sz_state = al(sizeof(unsigned) * 6 * nm), sz_coff = al(sizeof(long long) * (nm + 1)),
+                 sz_pb = al(sizeof(unsigned) * (nm + 1));
+    char *stage = nullptr;
+    GG_TRY(host_stage(c, sz_desc + sz_base + sz_state + sz_coff + sz_pb, &stage));
+    gg::MeshDesc *desc = (gg::MeshDesc *)stage;
+    long long *obj_base = (long long *)(stage + sz_desc);
+    unsigned *bstate = (unsigned *)(stage + sz_desc + sz_base);
+    long long *cells_off = (long long *)(stage + sz_desc + sz_base + sz_state);
+    unsigned *pair_base = (unsigned *)(stage + sz_desc + sz_base + sz_state + sz_coff);
+    obj_base[0] = 0;
     for (int m = 0; m < nm; ++m) {
         const grid_mesh &mesh = meshes[m];
         if (mesh.n < 0 || mesh.nverts < 0 || !valid_lambda(mesh.lambda)) return GRID_EINVAL;
@@ -945,7 +985,6 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
         if (obj_base[m + 1] > kInt32Max - 1) return GRID_EOVERFLOW;
     }
     const long long ntot = obj_base[nm];
-    std::vector<gg::MeshDesc> desc(nm);
     for (int m = 0; m < nm; ++m) {
         desc[m] = gg::MeshDesc{};
         desc[m].verts = meshes[m].verts;
@@ -961,9 +1000,9 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
     gg::MeshTab mt{(const gg::MeshDesc *)c->b_desc.ptr, (const long long *)c->b_base.ptr, nm};
     GG_TRY(reset_ctl(c));
     GG_CUDA(cudaMemsetAsync(c->b_state.ptr, 0, sizeof(unsigned) * 6 * nm, c->stream));
-    GG_CUDA(cudaMemcpyAsync(c->b_desc.ptr, desc.data(), sizeof(gg::MeshDesc) * nm, cudaMemcpyHostToDevice,
-                            c->stream));
-    GG_CUDA(cudaMemcpyAsync(c->b_base.ptr, obj_base.data(), sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice,
+    c->stage_busy = true;
+    GG_CUDA(cudaMemcpyAsync(c->b_desc.ptr, desc, sizeof(gg::MeshDesc) * nm, cudaMemcpyHostToDevice, c->stream));
+    GG_CUDA(cudaMemcpyAsync(c->b_base.ptr, obj_base, sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice,
                             c->stream));
 
     // a0: every mesh's scene bounds in one pass over the flattened triangles
@@ -971,14 +1010,12 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
         KernelScope ks(c, K_BOUNDS, 48.0 * ntot);
         GG_CUDA(gg::launch_bounds_batched(mt, ntot, (unsigned *)c->b_state.ptr, c->d_ctl, c->stream));
     }
-    std::vector<unsigned> bstate(6 * (size_t)nm);
-    GG_CUDA(cudaMemcpyAsync(bstate.data(), c->b_state.ptr, sizeof(unsigned) * 6 * nm, cudaMemcpyDeviceToHost,
-                            c->stream));
+    GG_CUDA(cudaMemcpyAsync(bstate, c->b_state.ptr, sizeof(unsigned) * 6 * nm, cudaMemcpyDeviceToHost, c->stream));
     GG_TRY(read_ctl(c));
     GG_TRY(ctl_error(c->h_ctl->err));
 
     // a1: each mesh's metadata; cell ids of mesh m start at cell_base[m]
-    std::vector<long long> cells_off(nm + 1, 0);
+    cells_off[0] = 0;
     long long cell_base = 0;
     for (int m = 0; m < nm; ++m) {
         float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
@@ -1000,8 +1037,7 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
         cells_off[m + 1] = cells_off[m] + infos[m].ncells + 1;
     }
     const long long ncells_all = cell_base;
-    GG_CUDA(cudaMemcpyAsync(c->b_desc.ptr, desc.data(), sizeof(gg::MeshDesc) * nm, cudaMemcpyHostToDevice,
-                            c->stream));
+    GG_CUDA(cudaMemcpyAsync(c->b_desc.ptr, desc, sizeof(gg::MeshDesc) * nm, cudaMemcpyHostToDevice, c->stream));
 
     // a2 + a3 over all objects: one scan, so each mesh's pairs follow the last
     const int64_t ctiles = (ntot + gg::COUNT_TILE - 1) / gg::COUNT_TILE;
@@ -1021,9 +1057,7 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
         KernelScope ks(c, K_COUNT, 64.0 * ntot);
         GG_CUDA(gg::launch_count_scan(ca, c->stream));
     }
-    std::vector<unsigned> pair_base(nm + 1, 0);
-    GG_CUDA(cudaMemcpyAsync(pair_base.data(), pair_base_d, sizeof(unsigned) * nm, cudaMemcpyDeviceToHost,
-                            c->stream));
+    GG_CUDA(cudaMemcpyAsync(pair_base, pair_base_d, sizeof(unsigned) * nm, cudaMemcpyDeviceToHost, c->stream));
     GG_TRY(read_ctl(c));
     GG_TRY(ctl_error(c->h_ctl->err));
     const int64_t NO = ntot > 0 ? (int64_t)c->h_ctl->nrefs : 0;
@@ -1084,16 +1118,16 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
         } else {
             GG_CUDA(cudaMemsetAsync(G, 0, (size_t)(ncells_all + 1) * sizeof(unsigned), c->stream));
         }
-        GG_CUDA(cudaMemcpyAsync(c->b_cellsoff.ptr, cells_off.data(), sizeof(long long) * (nm + 1),
-                                cudaMemcpyHostToDevice, c->stream));
-        GG_CUDA(cudaMemcpyAsync(pair_base_d, pair_base.data(), sizeof(unsigned) * nm, cudaMemcpyHostToDevice,
+        GG_CUDA(cudaMemcpyAsync(c->b_cellsoff.ptr, cells_off, sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice,
                                 c->stream));
+        GG_CUDA(cudaMemcpyAsync(pair_base_d, pair_base, sizeof(unsigned) * nm, cudaMemcpyHostToDevice, c->stream));
         {
             KernelScope ks(c, K_LOCALIZE, 8.0 * ncells_out);
             GG_CUDA(gg::launch_localize(G, (const long long *)c->b_cellsoff.ptr, pair_base_d, nm, ncells_out,
                                         (unsigned *)pc, c->stream));
         }
         GG_TRY(read_ctl(c));
+        c->stage_busy = false;
         return ctl_error(c->h_ctl->err);
     }();
     if (rc != GRID_OK) {

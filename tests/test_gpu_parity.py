@@ -372,6 +372,32 @@ def test_batched_rejects_bad_mesh(ctx):
         ctx.build_batched([(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam),
                            (dev(s.verts, torch.float32), dev(bad, torch.int32), s.lam)])
     assert e.value.code == -1
+    # the context's staging tables are reusable after the failed call
+    g = ctx.build_batched([(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)])
+    assert_grid_equal(g[0], oracle.build_grid(s.verts, s.tris, s.lam), "after a failed batch")
+
+
+def test_batched_sequence_views(ctx):
+    """The batch result indexes like a list (negative indices, slices) and its
+    per-mesh grids are views at cells_offsets / refs_offsets of the two
+    shared buffers."""
+    batch = _mixed_batch()
+    grids = ctx.build_batched([(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam) for s in batch])
+    n = len(batch)
+    assert grids[-1] is grids[n - 1] and [g.info.n for g in grids[1:3]] == [s.n for s in batch[1:3]]
+    with pytest.raises(IndexError):
+        grids[n]
+    with pytest.raises(IndexError):
+        grids[-n - 1]
+    assert grids.cells_offsets[0] == 0 and grids.refs_offsets[0] == 0
+    for m, g in enumerate(grids):
+        c0, r0 = grids.cells_offsets[m], grids.refs_offsets[m]
+        assert g.cells.data_ptr() == grids.cells.data_ptr() + 4 * c0
+        if g.info.nrefs:
+            assert g.refs.data_ptr() == grids.refs.data_ptr() + 4 * r0
+        if m + 1 < n:
+            assert grids.cells_offsets[m + 1] == c0 + g.info.ncells + 1
+            assert grids.refs_offsets[m + 1] == r0 + g.info.nrefs
 
 
 @pytest.mark.slow
