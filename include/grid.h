@@ -279,7 +279,10 @@ int grid_sort_pairs(grid_ctx *ctx, const int32_t *C, const int32_t *O, int64_t c
 
 /* a9, RunLengthEncode + NonEmptyCells + ExclusiveSum (Algorithm 1, Fig. 4d):
  * from the cell-sorted C (int32 [count], values in [0, ncells)) writes
- * cells (int32 [ncells + 1]), cells[c] = number of entries < c. */
+ * cells (int32 [ncells + 1]), cells[c] = number of entries < c.  A key
+ * >= ncells gives GRID_EINVAL; so does a key found out of order (unsorted
+ * input is caught where a block of keys leaves its expected cell range,
+ * not always: the contents of cells are then unspecified). */
 int grid_extract_ranges(grid_ctx *ctx, const int32_t *C_sorted, int64_t count, int64_t ncells,
                         int32_t *cells);
 

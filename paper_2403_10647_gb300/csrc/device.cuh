@@ -13,8 +13,8 @@ constexpr unsigned ERR_BADINDEX = 1u;   // triangle references a vertex outside 
 constexpr unsigned ERR_NONFINITE = 2u;  // NaN / Inf vertex coordinate
 constexpr unsigned ERR_OVERFLOW = 4u;   // a prefix sum passed INT32_MAX
 constexpr unsigned ERR_TIMEOUT = 8u;    // a bounded look-back wait gave up
-constexpr unsigned ERR_RANGE = 16u;     // a key outside [0, ncells) reached range extraction,
-                                        // or a sort scatter fell outside the output
+constexpr unsigned ERR_RANGE = 16u;     // a key outside [0, ncells) or out of order reached range
+                                        // extraction, or a sort scatter fell outside the output
 
 // Spin limit of every look-back wait (each iteration sleeps ~0.1-1 us).
 constexpr unsigned SPIN_LIMIT = 1u << 20;

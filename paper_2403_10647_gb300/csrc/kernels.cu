@@ -93,49 +93,50 @@ __host__ __device__ constexpr int padded() { return T + T / 32; }
 // MakeObjectIds + InclusiveSum for one pair tile, in shared memory: marks
 // each object whose pair segment starts inside [j0, j0 + cnt) at its start
 // position with its tile-local index, then an inclusive max-scan carries the
-// owning object forward.  Afterwards mark[pad32(e)] + (returned first object)
-// is the object of pair j0 + e.  mark holds padded<T>() entries; s_tmp
-// BLOCK / 32.
+// owning object forward.  Afterwards om[i] + (returned first object) is the
+// object of the thread's pair j0 + tid * ITEMS + i.  mark holds padded<T>()
+// entries and must be zero on entry (zero_marks, once per block); every
+// thread clears the entries it reads, so it is zero again on return and the
+// next tile needs no clearing pass.  s_tmp holds BLOCK / 32 entries.
+template <int BLOCK, int ITEMS>
+__device__ __forceinline__ void zero_marks(unsigned *mark)
+{
+    for (int p = threadIdx.x; p < padded<BLOCK * ITEMS>(); p += BLOCK) mark[p] = 0u;
+}
+
 template <int BLOCK, int ITEMS>
 __device__ __forceinline__ unsigned tile_objects(const ObjRec *__restrict__ recs,
                                                  const unsigned *__restrict__ tile_obj, unsigned t,
                                                  unsigned j0, unsigned cnt, unsigned *mark,
-                                                 unsigned *s_tmp)
+                                                 unsigned *s_tmp, unsigned (&om)[ITEMS])
 {
-    constexpr int T = BLOCK * ITEMS;
     constexpr int W = BLOCK / 32;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned of = tile_obj[t], ol = tile_obj[t + 1];
-    for (int p = tid; p < padded<T>(); p += BLOCK) mark[p] = 0u;
-    __syncthreads();
     for (unsigned o = of + 1u + tid; o <= ol; o += BLOCK) {
         const unsigned s = __ldg(&recs[o].start);
         const unsigned p = s - j0;
         if (s >= j0 && p < cnt) mark[pad32(p)] = o - of;
     }
     __syncthreads();
-    unsigned v[ITEMS];
     unsigned m = 0;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        m = max(m, mark[pad32(tid * ITEMS + i)]);
-        v[i] = m;
+        const unsigned e = pad32(tid * ITEMS + i);
+        m = max(m, mark[e]);
+        mark[e] = 0u;
+        om[i] = m;
     }
-    unsigned inc = warp_incl_max(m);
+    const unsigned inc = warp_incl_max(m);
     if (lane == 31) s_tmp[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        unsigned x = lane < W ? s_tmp[lane] : 0u;
-        x = warp_incl_max(x);
-        if (lane < W) s_tmp[lane] = x;
-    }
     __syncthreads();
     unsigned prev = __shfl_up_sync(0xffffffffu, inc, 1);
     if (lane == 0) prev = 0u;
-    if (w > 0) prev = max(prev, s_tmp[w - 1]);
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) mark[pad32(tid * ITEMS + i)] = max(v[i], prev);
-    __syncthreads();
+    for (int ww = 0; ww < W - 1; ++ww)
+        if (ww < w) prev = max(prev, s_tmp[ww]);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) om[i] = max(om[i], prev);
     return of;
 }
 
@@ -164,7 +165,7 @@ __device__ __forceinline__ int mesh_of(const MeshTab &mt, long long o)
 // In a batched build (mt.md set) each object's mesh supplies the grid
 // strides, the key offset cell_base and the object-id offset.
 template <int ITEMS>
-__device__ __forceinline__ void gen_blocked(const ObjRec *__restrict__ recs, unsigned of, const unsigned *mark,
+__device__ __forceinline__ void gen_blocked(const ObjRec *__restrict__ recs, unsigned of, const unsigned (&om)[ITEMS],
                                             unsigned j0, unsigned cnt, unsigned res_x, unsigned res_y,
                                             const MeshTab &mt, unsigned (&keys)[ITEMS], unsigned (&objs)[ITEMS])
 {
@@ -177,7 +178,7 @@ __device__ __forceinline__ void gen_blocked(const ObjRec *__restrict__ recs, uns
         keys[i] = 0u;
         objs[i] = 0u;
         if (e < cnt) {
-            const unsigned oe = of + mark[pad32(e)];
+            const unsigned oe = of + om[i];
             if (i == 0 || oe != o) {
                 o = oe;
                 const uint4 r = __ldg(reinterpret_cast<const uint4 *>(recs) + o);
@@ -463,9 +464,12 @@ __global__ void __launch_bounds__(BLOCK) emit_kernel(EmitArgs a)
     const unsigned t = blockIdx.x;
     const unsigned j0 = t * (unsigned)T;
     const unsigned cnt = min((unsigned)T, a.count - j0);
-    const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
+    zero_marks<BLOCK, ITEMS>(s_mark);
+    __syncthreads();
+    unsigned om[ITEMS];
+    const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp, om);
     unsigned keys[ITEMS], objs[ITEMS];
-    gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
+    gen_blocked<ITEMS>(a.recs, of, om, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -620,10 +624,12 @@ __global__ void __launch_bounds__(BLOCK) cull_emit_kernel(CullArgs a)
     const unsigned ntiles = (a.count + T - 1) / T;
     const unsigned j0 = t * (unsigned)T;
     const unsigned cnt = min((unsigned)T, a.count - j0);
-    const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
+    zero_marks<BLOCK, ITEMS>(s_mark);
+    __syncthreads();
     {
-        unsigned keys[ITEMS], objs[ITEMS];
-        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, MeshTab{}, keys, objs);
+        unsigned om[ITEMS], keys[ITEMS], objs[ITEMS];
+        const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp, om);
+        gen_blocked<ITEMS>(a.recs, of, om, j0, cnt, a.res_x, a.res_y, MeshTab{}, keys, objs);
         __syncthreads();   // every thread is done with the object marks
         // the thread's own items go to shared memory: the test loop below is
         // not unrolled (one copy of the test) and no item stays in registers
@@ -832,30 +838,52 @@ __global__ void wait_selftest_kernel(const unsigned *col, Ctl *ctl, unsigned *ou
 }
 
 template <int BLOCK, int ITEMS, int RBITS, int SRC>
-__global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
+__global__ void __launch_bounds__(BLOCK, SRC == SRC_GEN ? GEN_MIN_BLOCKS : 2048 / BLOCK) upsweep_kernel(UpArgs a)
 {
     constexpr int T = BLOCK * ITEMS;
     constexpr int R = 1 << RBITS;
     extern __shared__ __align__(16) unsigned smem[];
-    unsigned *s_cnt = smem;                          // [R] this tile's digit counts
-    unsigned *s_run = s_cnt + R;                     // [R] counts of the group's tiles so far
+    unsigned *s_cnt2 = smem;                         // [2][R] digit counts of even / odd tiles
+    unsigned *s_run = s_cnt2 + 2 * R;                // [R] counts of the group's tiles so far
     unsigned *s_mark = s_run + R;                    // [padded T] object marks (generated pairs)
     __shared__ unsigned s_tmp[BLOCK / 32];
     const int tid = threadIdx.x;
     const unsigned g = blockIdx.x;
     const unsigned t0 = g * GROUP_TILES, t1 = min(t0 + GROUP_TILES, a.ntiles);
     const unsigned sh = a.shift, mk = (1u << a.bits) - 1u;
-    for (int i = tid; i < 2 * R; i += BLOCK) smem[i] = 0u;
+    for (int i = tid; i < 3 * R; i += BLOCK) smem[i] = 0u;
+    if (SRC == SRC_GEN) zero_marks<BLOCK, ITEMS>(s_mark);
     __syncthreads();
+
+    // a tile's keys, 16 bytes per load where the whole run is in range
+    auto load_keys = [&](unsigned t, unsigned (&k)[ITEMS]) {
+        const unsigned j0 = t * (unsigned)T;
+        const unsigned cnt = min((unsigned)T, a.count - j0);
+#pragma unroll
+        for (int i = 0; i < ITEMS; i += 4) {
+            const unsigned e = tid * ITEMS + i;
+            if (e + 3 < cnt) {
+                const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(a.keys_in + j0 + e));
+                k[i] = v.x;
+                k[i + 1] = v.y;
+                k[i + 2] = v.z;
+                k[i + 3] = v.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) k[i + q] = e + q < cnt ? a.keys_in[j0 + e + q] : 0u;
+            }
+        }
+    };
+    unsigned keys[ITEMS];
 
     for (unsigned t = t0; t < t1; ++t) {
         const unsigned j0 = t * (unsigned)T;
         const unsigned cnt = min((unsigned)T, a.count - j0);
-        unsigned keys[ITEMS];
+        unsigned *s_cnt = s_cnt2 + ((t - t0) & 1u) * R;
         if (SRC == SRC_GEN) {
-            unsigned objs[ITEMS];
-            const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp);
-            gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
+            unsigned om[ITEMS], objs[ITEMS];
+            const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, t, j0, cnt, s_mark, s_tmp, om);
+            gen_blocked<ITEMS>(a.recs, of, om, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
             if (a.gen_keys) {
                 // store the object-order pairs once, for the first downsweep
                 // to read instead of generating them a second time
@@ -880,33 +908,23 @@ __global__ void __launch_bounds__(BLOCK) upsweep_kernel(UpArgs a)
                 }
             }
         } else {
-#pragma unroll
-            for (int i = 0; i < ITEMS; i += 4) {
-                const unsigned e = tid * ITEMS + i;
-                if (e + 3 < cnt) {
-                    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(a.keys_in + j0 + e));
-                    keys[i] = v.x;
-                    keys[i + 1] = v.y;
-                    keys[i + 2] = v.z;
-                    keys[i + 3] = v.w;
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) keys[i + q] = e + q < cnt ? a.keys_in[j0 + e + q] : 0u;
-                }
-            }
+            load_keys(t, keys);
         }
         const unsigned nv = cnt > (unsigned)(tid * ITEMS) ? min((unsigned)ITEMS, cnt - tid * ITEMS) : 0u;
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i)
             if ((unsigned)i < nv) atomicAdd(&s_cnt[(keys[i] >> sh) & mk], 1u);
         __syncthreads();
+        // one barrier per tile: the next tile counts into the other buffer,
+        // and this one is next counted into two tiles on, after the next
+        // barrier (each thread clears the digits it reads)
         for (int d = tid; d < R; d += BLOCK) {
             a.intra[(size_t)t * R + d] = (unsigned short)s_run[d];
             s_run[d] += s_cnt[d];
             s_cnt[d] = 0u;
         }
-        __syncthreads();
     }
+    unsigned *s_cnt = s_cnt2;
 
     // the group's offsets: decoupled look-back across groups, per digit
     for (int d = tid; d < R; d += BLOCK) {
@@ -1034,10 +1052,11 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
     // item i of this lane is element e = w * 32 * ITEMS + i * 32 + lane
     unsigned keys[ITEMS];
     if (IN == IN_GEN) {
-        unsigned objs[ITEMS];
+        unsigned om[ITEMS], objs[ITEMS];
+        zero_marks<BLOCK, ITEMS>(s_mark);
         __syncthreads();
-        const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, tile, j0, cnt, s_mark, s_tmp);
-        gen_blocked<ITEMS>(a.recs, of, s_mark, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
+        const unsigned of = tile_objects<BLOCK, ITEMS>(a.recs, a.tile_obj, tile, j0, cnt, s_mark, s_tmp, om);
+        gen_blocked<ITEMS>(a.recs, of, om, j0, cnt, a.res_x, a.res_y, a.mt, keys, objs);
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) s_elem[pad16(tid * ITEMS + i)] = pack_kv(keys[i], objs[i]);
@@ -1231,10 +1250,17 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
     const unsigned long long d0 = (unsigned long long)blockIdx.x * D;
     const unsigned long long d1 = min(d0 + D, M);
     const unsigned long long i0 = a.splits[blockIdx.x], i1 = a.splits[blockIdx.x + 1];
+    // splits out of order, or more keys than merged items, come only from
+    // keys that are not sorted: report them and touch nothing (the sizes
+    // below would wrap)
+    if (i1 < i0 || i1 - i0 > d1 - d0) {
+        if (threadIdx.x == 0) atomicOr(&a.ctl->err, ERR_RANGE);
+        return;
+    }
     // every key before i0 is below c0 and every key from i1 on is at least
     // c1, so G[c] = i0 + (keys of this block below c); cell ids fit 32 bits
     const unsigned c0 = (unsigned)(d0 - i0), c1 = (unsigned)(d1 - i1);
-    const unsigned na = (unsigned)(i1 - i0), nc = c1 - c0, nd = na + nc;
+    const unsigned na = (unsigned)(i1 - i0), nc = c1 - c0;
     // the block's keys: 16-byte loads over the aligned middle (many bytes in
     // flight per thread), single words at the ragged ends; nothing outside
     // [i0, i1) is read
@@ -1469,7 +1495,7 @@ static cudaError_t launch_up_t(const UpArgs &a, cudaStream_t s)
 {
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
     auto k = upsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, SRC>;
-    const size_t smem = sizeof(unsigned) * (2 * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
+    const size_t smem = sizeof(unsigned) * (3 * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
     static std::atomic<unsigned long long> configured{0};
     if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
     const unsigned groups = (a.ntiles + GROUP_TILES - 1) / GROUP_TILES;

@@ -22,12 +22,19 @@ namespace gg {
 #ifndef GG_GROUP_TILES
 #define GG_GROUP_TILES 16
 #endif
+#ifndef GG_GEN_MIN_BLOCKS
+#define GG_GEN_MIN_BLOCKS 6
+#endif
 constexpr int COUNT_BLOCK = 256;
 constexpr int COUNT_TILE = 2048;
 constexpr int PAIR_BLOCK = GG_PAIR_BLOCK;
 constexpr int PAIR_TILE = GG_PAIR_BLOCK * GG_PAIR_ITEMS;
 constexpr int PASS_MIN_BLOCKS = GG_PASS_MIN_BLOCKS;
 constexpr int GROUP_TILES = GG_GROUP_TILES;   // tiles per upsweep block
+// resident blocks per SM the pair-generating upsweep is compiled for: its
+// per-tile chain (object marks, records, stores) is latency-bound, so more
+// blocks in flight beat the few registers spilled
+constexpr int GEN_MIN_BLOCKS = GG_GEN_MIN_BLOCKS;
 static_assert(GROUP_TILES * PAIR_TILE <= 65536, "tile offsets inside a group fit 16 bits");
 constexpr int EXTRACT_BLOCK = 256;
 constexpr int EXTRACT_TILE = 2048;

@@ -152,6 +152,38 @@ def test_extract_ranges(ctx, ncells, count):
     assert np.array_equal(host(G), oracle.ranges(C, ncells))
 
 
+@pytest.mark.parametrize("pattern", ["one_cell", "ends", "long_runs", "first_and_last_cell", "every_cell"])
+def test_extract_ranges_patterns(ctx, pattern):
+    """Runs longer than an extraction block (2,048 merged items), gaps of a
+    million empty cells, keys only in the first and last cells."""
+    g = np.random.Generator(np.random.Philox(4711))
+    ncells = 1_000_003
+    if pattern == "one_cell":
+        C = np.full(50_000, ncells // 2, np.int32)
+    elif pattern == "ends":
+        C = np.repeat(np.array([0, 1, ncells - 2, ncells - 1], np.int32), [3, 5000, 7, 4100])
+    elif pattern == "long_runs":
+        C = np.sort(g.choice(ncells, 40, replace=False).astype(np.int32).repeat(g.integers(1, 9000, 40)))
+    elif pattern == "first_and_last_cell":
+        C = np.array([0] * 3000 + [ncells - 1] * 2, np.int32)
+    else:
+        C = np.arange(ncells, dtype=np.int32)
+    G = ctx.extract_ranges(dev(C, torch.int32), ncells)
+    assert np.array_equal(host(G), oracle.ranges(C, ncells)), pattern
+
+
+def test_extract_ranges_rejects_unsorted_keys(ctx):
+    """Keys out of order (a caller's mistake) are reported, not read as a
+    grid, and the context stays usable."""
+    import paper_2403_10647_gb300 as pg
+    g = np.random.Generator(np.random.Philox(4712))
+    C = g.integers(0, 1000, 100_000).astype(np.int32)
+    with pytest.raises(pg.GridError):
+        ctx.extract_ranges(dev(C, torch.int32), 1000)
+    C.sort()
+    assert np.array_equal(host(ctx.extract_ranges(dev(C, torch.int32), 1000)), oracle.ranges(C, 1000))
+
+
 @pytest.mark.parametrize("offset", [1, 2, 3, 4])
 def test_extract_ranges_unaligned_input(ctx, offset):
     """A caller's sorted keys may start off a 16-byte boundary (a slice of a
