@@ -292,6 +292,51 @@ constexpr unsigned long long LB64_AGG = 1ull << 62;
 constexpr unsigned long long LB64_PREFIX = 2ull << 62;
 constexpr unsigned long long LB64_VALUE = (1ull << 62) - 1ull;
 
+// Decoupled look-back of tile t over 64-bit status words (flag | value), run
+// by one whole warp: publishes t's aggregate, reads 32 predecessors per round
+// trip (lane q reads tile k - q), adds every aggregate up to the nearest
+// inclusive prefix, then publishes t's own inclusive prefix.  A word not yet
+// published ahead of that prefix means polling the window again, at most
+// SPIN_LIMIT times (then ERR_TIMEOUT and the partial sum).  Returns the
+// exclusive prefix in every lane.
+__device__ __forceinline__ unsigned long long warp_lookback64(unsigned long long *st, unsigned t,
+                                                              unsigned long long total, Ctl *ctl)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long excl = 0;
+    if (t == 0) {
+        if (lane == 0) st_relaxed_u64(&st[0], LB64_PREFIX | total);
+        return 0ull;
+    }
+    if (lane == 0) st_relaxed_u64(&st[t], LB64_AGG | total);
+    long long k = (long long)t - 1;
+    unsigned spins = 0;
+    while (true) {
+        const long long idx = k - lane;
+        const unsigned long long v = idx >= 0 ? ld_relaxed_u64(&st[idx]) : LB64_PREFIX;
+        const unsigned pre = __ballot_sync(0xffffffffu, (v & LB64_PREFIX) != 0ull);
+        const unsigned zero = __ballot_sync(0xffffffffu, v == 0ull);
+        const int p = pre ? __ffs(pre) - 1 : 32;                // nearest prefix in the window
+        const unsigned upto = p < 31 ? (2u << p) - 1u : 0xffffffffu;
+        if (zero & upto) {                                       // a nearer tile has not published
+            if (++spins > SPIN_LIMIT) {
+                if (lane == 0) atomicOr(&ctl->err, ERR_TIMEOUT);
+                break;
+            }
+            if (spins > 8) __nanosleep(64);
+            continue;
+        }
+        unsigned long long part = lane <= p ? (v & LB64_VALUE) : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        excl += part;
+        if (p < 32) break;
+        k -= 32;
+    }
+    if (lane == 0) st_relaxed_u64(&st[t], LB64_PREFIX | ((excl + total) & LB64_VALUE));
+    return excl;
+}
+
 template <int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
 {
@@ -378,34 +423,13 @@ __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) s_pref[tid * ITEMS + i] += texcl;
 
-    if (tid == 0) {
-        unsigned long long *st = a.status;
-        unsigned long long excl = 0;
-        if (tile == 0) {
-            st_relaxed_u64(&st[0], LB64_PREFIX | total);
-        } else {
-            st_relaxed_u64(&st[tile], LB64_AGG | total);
-            long long k = (long long)tile - 1;
-            unsigned spins = 0;
-            while (k >= 0) {
-                const unsigned long long v = ld_relaxed_u64(&st[k]);
-                if (v == 0ull) {
-                    if (++spins > SPIN_LIMIT) {
-                        atomicOr(&a.ctl->err, ERR_TIMEOUT);
-                        break;
-                    }
-                    if (spins > 8) __nanosleep(64);
-                    continue;
-                }
-                excl += v & LB64_VALUE;
-                if (v & LB64_PREFIX) break;
-                --k;
-            }
-            st_relaxed_u64(&st[tile], LB64_PREFIX | ((excl + total) & LB64_VALUE));
+    if (tid < 32) {
+        const unsigned long long excl = warp_lookback64(a.status, tile, total, a.ctl);
+        if (tid == 0) {
+            s_excl = excl;
+            if (excl + total > 0x7FFFFFFFull) atomicOr(&a.ctl->err, ERR_OVERFLOW);
+            if (base + T >= a.n) a.ctl->nrefs = excl + total;
         }
-        s_excl = excl;
-        if (excl + total > 0x7FFFFFFFull) atomicOr(&a.ctl->err, ERR_OVERFLOW);
-        if (base + T >= a.n) a.ctl->nrefs = excl + total;
     }
     __syncthreads();
     const unsigned long long excl = s_excl;
@@ -727,33 +751,12 @@ __global__ void __launch_bounds__(BLOCK) cull_emit_kernel(CullArgs a)
             ++pos;
         }
     }
-    if (tid == 0) {
-        unsigned long long *st = a.status;
-        unsigned long long excl = 0;
-        if (t == 0) {
-            st_relaxed_u64(&st[0], LB64_PREFIX | total);
-        } else {
-            st_relaxed_u64(&st[t], LB64_AGG | total);
-            long long k = (long long)t - 1;
-            unsigned spins = 0;
-            while (k >= 0) {
-                const unsigned long long v = ld_relaxed_u64(&st[k]);
-                if (v == 0ull) {
-                    if (++spins > SPIN_LIMIT) {
-                        atomicOr(&a.ctl->err, ERR_TIMEOUT);
-                        break;
-                    }
-                    if (spins > 8) __nanosleep(64);
-                    continue;
-                }
-                excl += v & LB64_VALUE;
-                if (v & LB64_PREFIX) break;
-                --k;
-            }
-            st_relaxed_u64(&st[t], LB64_PREFIX | ((excl + total) & LB64_VALUE));
+    if (tid < 32) {
+        const unsigned long long excl = warp_lookback64(a.status, t, total, a.ctl);
+        if (tid == 0) {
+            s_excl = excl;
+            if (t == ntiles - 1) a.ctl->nkept = excl + total;
         }
-        s_excl = excl;
-        if (t == ntiles - 1) a.ctl->nkept = excl + total;
     }
     __syncthreads();
     const unsigned long long base = s_excl;
