@@ -423,7 +423,7 @@ int grid_serve_get_stats(grid_server *srv, grid_serve_stats *out, int reset);
  * (different streams or threads at the same time) race and must be
  * serialised by the caller.
  *
- * Limit: count + ncells + 1 <= 2^18 * 2048 (about 5.4e8); larger requests
+ * Limit: count + ncells + 1 <= 2^18 * 4096 (about 1.07e9); larger requests
  * return GRID_ELIMIT without touching the GPU.  GRID_EINVAL for bad
  * arguments or a key >= ncells, GRID_ECUDA for a failed CUDA call. */
 int grid_extract_ranges_noalloc(const int32_t *C_sorted, int64_t count, int64_t ncells, int32_t *cells,

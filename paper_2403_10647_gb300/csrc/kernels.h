@@ -37,7 +37,7 @@ constexpr int GROUP_TILES = GG_GROUP_TILES;   // tiles per upsweep block
 constexpr int GEN_MIN_BLOCKS = GG_GEN_MIN_BLOCKS;
 static_assert(GROUP_TILES * PAIR_TILE <= 65536, "tile offsets inside a group fit 16 bits");
 constexpr int EXTRACT_BLOCK = 256;
-constexpr int EXTRACT_TILE = 2048;
+constexpr int EXTRACT_TILE = 4096;
 
 enum { SRC_MEM = 0, SRC_GEN = 1 };
 

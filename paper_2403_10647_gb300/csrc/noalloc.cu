@@ -22,7 +22,7 @@ namespace {
 
 // Split table capacity: one entry per extraction block plus one.  A block
 // covers gg::EXTRACT_TILE merged items (keys + cells + 1), so this bounds
-// count + ncells + 1 by NOALLOC_MAX_BLOCKS * EXTRACT_TILE (about 5.4e8).
+// count + ncells + 1 by NOALLOC_MAX_BLOCKS * EXTRACT_TILE (about 1.07e9).
 constexpr unsigned long long NOALLOC_MAX_BLOCKS = 1ull << 18;
 
 static __device__ __align__(256) unsigned g_noalloc_splits[NOALLOC_MAX_BLOCKS + 1];

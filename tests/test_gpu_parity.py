@@ -154,7 +154,7 @@ def test_extract_ranges(ctx, ncells, count):
 
 @pytest.mark.parametrize("pattern", ["one_cell", "ends", "long_runs", "first_and_last_cell", "every_cell"])
 def test_extract_ranges_patterns(ctx, pattern):
-    """Runs longer than an extraction block (2,048 merged items), gaps of a
+    """Runs longer than an extraction block (4,096 merged items), gaps of a
     million empty cells, keys only in the first and last cells."""
     g = np.random.Generator(np.random.Philox(4711))
     ncells = 1_000_003
