@@ -776,11 +776,12 @@ __global__ void __launch_bounds__(BLOCK) cull_emit_kernel(CullArgs a)
 // ---------------------------------------------------------------------------
 //
 // Upsweep of pass p: per tile of PAIR_TILE pairs, the count of each digit;
-// per group of GROUP_TILES consecutive tiles, one block walks its tiles in
-// order and writes each tile's digit offsets inside the group, then a
-// decoupled look-back across groups yields each group's offsets.  Groups
-// start GROUP_TILES times less often than tiles, so look-back chains stay
-// short at GB300's tile rate.  The last group's inclusive prefixes are the
+// per group of gtiles consecutive tiles, one block walks its tiles in order
+// and writes each tile's digit offsets inside the group, then a decoupled
+// look-back across groups yields each group's offsets.  Groups start gtiles
+// times less often than tiles, so look-back chains stay short at GB300's
+// tile rate; small passes use fewer tiles per group (down to one) so that
+// their groups still fill the GPU.  The last group's inclusive prefixes are the
 // pass's digit totals; its block scans them into the digit starts.  The
 // first pass's upsweep generates the pairs (no pair array exists yet) and
 // stores them for the first downsweep.
@@ -852,7 +853,7 @@ __global__ void __launch_bounds__(BLOCK, SRC == SRC_GEN ? GEN_MIN_BLOCKS : 2048 
     __shared__ unsigned s_tmp[BLOCK / 32];
     const int tid = threadIdx.x;
     const unsigned g = blockIdx.x;
-    const unsigned t0 = g * GROUP_TILES, t1 = min(t0 + GROUP_TILES, a.ntiles);
+    const unsigned t0 = g * a.gtiles, t1 = min(t0 + a.gtiles, a.ntiles);
     const unsigned sh = a.shift, mk = (1u << a.bits) - 1u;
     for (int i = tid; i < 3 * R; i += BLOCK) smem[i] = 0u;
     if (SRC == SRC_GEN) zero_marks<BLOCK, ITEMS>(s_mark);
@@ -1015,7 +1016,7 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 
 template <int BLOCK, int ITEMS, int RBITS, int IN>
-__global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownArgs a, unsigned ntiles)
+__global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownArgs a, unsigned gtiles)
 {
     constexpr int W = BLOCK / 32;
     constexpr int T = BLOCK * ITEMS;
@@ -1041,8 +1042,7 @@ __global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownA
     const unsigned ltmask = lanemask_lt();
     const unsigned bit = 1u << lane;
     const unsigned tile = blockIdx.x;
-    (void)ntiles;
-    const unsigned group = tile / GROUP_TILES;
+    const unsigned group = tile / gtiles;   // the upsweep group holding this tile
     const unsigned j0 = tile * (unsigned)T;
     const unsigned cnt = min((unsigned)T, a.count - j0);
     for (int i = tid; i < W * R / 2; i += BLOCK) s_wh32[i] = 0u;
@@ -1501,22 +1501,29 @@ static cudaError_t launch_up_t(const UpArgs &a, cudaStream_t s)
     const size_t smem = sizeof(unsigned) * (3 * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
     static std::atomic<unsigned long long> configured{0};
     if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
-    const unsigned groups = (a.ntiles + GROUP_TILES - 1) / GROUP_TILES;
+    if (a.gtiles < 1 || a.gtiles > (unsigned)GROUP_TILES) return cudaErrorInvalidValue;
+    const unsigned groups = (a.ntiles + a.gtiles - 1) / a.gtiles;
     k<<<groups, PAIR_BLOCK, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int RBITS, int IN>
-static cudaError_t launch_down_t(const DownArgs &a, unsigned ntiles, int nsm, cudaStream_t s)
+static cudaError_t launch_down_t(const DownArgs &a, unsigned ntiles, unsigned gtiles, cudaStream_t s)
 {
     constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
     auto k = downsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, IN>;
     constexpr size_t smem = down_smem_bytes<PAIR_BLOCK, ITEMS, RBITS>();
-    (void)nsm;
     static std::atomic<unsigned long long> configured{0};
     if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
-    k<<<ntiles, PAIR_BLOCK, smem, s>>>(a, ntiles);
+    k<<<ntiles, PAIR_BLOCK, smem, s>>>(a, gtiles);
     return cudaGetLastError();
+}
+
+unsigned group_tiles(unsigned ntiles, int nsm)
+{
+    // about 8 blocks per SM before groups grow past one tile
+    const unsigned per = ntiles / (unsigned)(8 * (nsm > 0 ? nsm : 1));
+    return per < 1u ? 1u : (per > (unsigned)GROUP_TILES ? (unsigned)GROUP_TILES : per);
 }
 
 cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s)
@@ -1536,12 +1543,14 @@ cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s)
 #undef GG_UP
 }
 
-cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, int nsm, cudaStream_t s)
+cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, unsigned gtiles, cudaStream_t s)
 {
     if (ntiles == 0) return cudaSuccess;
+    if (gtiles < 1 || gtiles > (unsigned)GROUP_TILES) return cudaErrorInvalidValue;
 #define GG_DOWN(RB)                                                        \
     case RB:                                                               \
-        return in == IN_GEN ? launch_down_t<RB, IN_GEN>(a, ntiles, nsm, s) : launch_down_t<RB, IN_PAIR>(a, ntiles, nsm, s);
+        return in == IN_GEN ? launch_down_t<RB, IN_GEN>(a, ntiles, gtiles, s)  \
+                            : launch_down_t<RB, IN_PAIR>(a, ntiles, gtiles, s);
     switch (rbits) {
         GG_DOWN(8)
         GG_DOWN(9)

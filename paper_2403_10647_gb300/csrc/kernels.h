@@ -30,7 +30,7 @@ constexpr int COUNT_TILE = 2048;
 constexpr int PAIR_BLOCK = GG_PAIR_BLOCK;
 constexpr int PAIR_TILE = GG_PAIR_BLOCK * GG_PAIR_ITEMS;
 constexpr int PASS_MIN_BLOCKS = GG_PASS_MIN_BLOCKS;
-constexpr int GROUP_TILES = GG_GROUP_TILES;   // tiles per upsweep block
+constexpr int GROUP_TILES = GG_GROUP_TILES;   // most tiles per upsweep block
 // resident blocks per SM the pair-generating upsweep is compiled for: its
 // per-tile chain (object marks, records, stores) is latency-bound, so more
 // blocks in flight beat the few registers spilled
@@ -106,7 +106,7 @@ struct CullArgs {
 };
 
 // Upsweep of one radix-sort pass: digit counts per tile, offsets of each
-// tile inside its group of GROUP_TILES tiles, offsets of each group, and,
+// tile inside its group of gtiles tiles, offsets of each group, and,
 // from the last group's inclusive prefixes, the pass's digit starts.
 struct UpArgs {
     const unsigned *keys_in;        // SRC_MEM
@@ -125,6 +125,7 @@ struct UpArgs {
     unsigned *status;               // [ngroups][2^RBITS] look-back words, zero on entry
     unsigned *dbase;                // [2^bits] out: the pass's digit starts (written by the last group)
     Ctl *ctl;
+    unsigned gtiles;                // tiles per group, 1 .. GROUP_TILES (group_tiles)
 };
 
 // Downsweep of one pass: stable rank and scatter of each tile.
@@ -193,8 +194,13 @@ cudaError_t launch_wait_selftest(const unsigned *col, Ctl *ctl, unsigned *out, c
 // pairs C[start ..], O[start ..] (single mesh).
 cudaError_t launch_make_pairs_per_object(const ObjRec *recs, long long n, unsigned res_x, unsigned res_y,
                                          unsigned count, unsigned *C, unsigned *O, Ctl *ctl, cudaStream_t s);
+// Tiles per upsweep group for a pass of ntiles tiles on nsm SMs: GROUP_TILES
+// when there are enough groups to fill the GPU, fewer (down to 1) when the
+// groups would not: a group's tiles are walked by one block in sequence.
+unsigned group_tiles(unsigned ntiles, int nsm);
 cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s);
-cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, int nsm, cudaStream_t s);
+// gtiles: the tiles per group of the pass's upsweep
+cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, unsigned gtiles, cudaStream_t s);
 unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells);
 cudaError_t launch_extract_split(const ExtractArgs &a, cudaStream_t s);
 cudaError_t launch_extract(const ExtractArgs &a, cudaStream_t s);

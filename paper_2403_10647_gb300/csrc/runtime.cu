@@ -341,7 +341,8 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
                const unsigned *keys_in, const unsigned *vals_in, unsigned *keys_last, unsigned *vals_last)
 {
     const unsigned ntiles = pair_tiles(count);
-    const unsigned ngroups = (ntiles + gg::GROUP_TILES - 1) / gg::GROUP_TILES;
+    const unsigned gtiles = gg::group_tiles(ntiles, c->nsm);
+    const unsigned ngroups = (ntiles + gtiles - 1) / gtiles;
     const int R = 1 << sc.rbits;
     const size_t elem = (size_t)count * sizeof(unsigned);
     // generated pairs are stored once by the first upsweep unless the first
@@ -385,6 +386,7 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         u.gen_vals = first ? gv : nullptr;
         u.count = count;
         u.ntiles = ntiles;
+        u.gtiles = gtiles;
         u.shift = sc.shift[p];
         u.bits = sc.bits[p];
         u.intra = (unsigned short *)c->intra.ptr;
@@ -417,7 +419,7 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         a.intra = (const unsigned short *)c->intra.ptr;
         a.ctl = c->d_ctl;
         KernelScope ks(c, gen_down ? K_DOWN_GEN : K_DOWN, gen_down ? 16.0 * nobj + 8.0 * count : 16.0 * count);
-        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_down ? gg::IN_GEN : gg::IN_PAIR, ntiles, c->nsm, c->stream));
+        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_down ? gg::IN_GEN : gg::IN_PAIR, ntiles, gtiles, c->stream));
     }
     return GRID_OK;
 }
