@@ -62,6 +62,8 @@ def parse():
                     help="time the culled build (false-intersection culling before the sort) instead")
     ap.add_argument("--pair-gen", default=None, choices=["fused", "regen", "emit", "per_object"],
                     help="fix the pair generation instead of autotuning it")
+    ap.add_argument("--tile-shape", default="256x12", choices=["256x12", "384x8"],
+                    help="block shape of the radix-sort kernels of the timed builds")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-threads", type=int, default=2,
                     help="host threads issuing grid_build_host calls for the end-to-end number")
@@ -491,7 +493,8 @@ def run_ours(args, rank, world, local):
             dist.barrier()
 
     scene = make_scene(args.workload)
-    ctx = pg.Context(local, radix_bits=args.radix_bits, pair_gen=args.pair_gen or "fused", cull=args.cull)
+    ctx = pg.Context(local, radix_bits=args.radix_bits, pair_gen=args.pair_gen or "fused", cull=args.cull,
+                     tile_shape=args.tile_shape)
     v = torch.from_numpy(scene.verts).cuda()
     t = torch.from_numpy(scene.tris).cuda()
     torch.cuda.synchronize()
@@ -547,7 +550,7 @@ def run_ours(args, rank, world, local):
         ht = torch.from_numpy(scene.tris).pin_memory()
         nth = max(1, args.e2e_threads)
         ctxs = [ctx] + [pg.Context(local, radix_bits=args.radix_bits, pair_gen=args.pair_gen or "fused",
-                                   cull=args.cull) for _ in range(nth - 1)]
+                                   cull=args.cull, tile_shape=args.tile_shape) for _ in range(nth - 1)]
         outs = [(torch.empty(info.ncells + 1, dtype=torch.int32).pin_memory(),
                  torch.empty(max(nrefs, 1), dtype=torch.int32).pin_memory()) for _ in range(nth)]
         streams = [torch.cuda.Stream() for _ in range(nth)]
@@ -654,10 +657,11 @@ def run_ours(args, rank, world, local):
         "config": {"workload": args.workload, "n_tris": scene.n, "lambda": scene.lam, "grid": list(info.res),
                    "ncells": info.ncells, "nrefs": nrefs, "key_bits": info.key_bits,
                    "radix_bits": args.radix_bits, "sort_passes": sort_passes(info.key_bits, args.radix_bits),
-                   "pair_gen": args.pair_gen or "fused", "cull": bool(args.cull),
-                   "autotune_choice": f"{tuned['radix_bits']}/{tuned['pair_gen']}" if tuned else None,
-                   "autotune_ms": ({f"{rb}/{m}": round(ms, 4) for (rb, m), ms in tuned["times_ms"].items()}
-                                   if tuned else None),
+                   "pair_gen": args.pair_gen or "fused", "cull": bool(args.cull), "tile_shape": args.tile_shape,
+                   "autotune_choice": (f"{tuned['radix_bits']}/{tuned['pair_gen']}/{tuned['tile_shape']}"
+                                       if tuned else None),
+                   "autotune_ms": ({(k if isinstance(k, str) else f"{k[0]}/{k[1]}"): round(ms, 4)
+                                    for k, ms in tuned["times_ms"].items()} if tuned else None),
                    "l2": l2_note,
                    "parallelism": f"replicas{world}"},
         "builds_per_s": world * args.steps / (ms_max / 1e3),

@@ -110,7 +110,11 @@ typedef struct {
                              sort (grid_cull_pairs' test); single-mesh builds only.  The grid is
                              then the culled grid: nrefs counts the kept pairs.  0: box placement
                              (Algorithm 1 as published, the default) */
-    int32_t reserved[5];
+    int32_t tile_shape;   /* block shape of the radix-sort kernels; both sort 3,072-pair tiles and
+                             give the same grid.  0: 256 threads x 12 pairs (the default; fastest
+                             on large, dense scenes), 1: 384 threads x 8 pairs (more warps per tile;
+                             faster on sparse and small scenes).  grid_ctx_autotune picks one */
+    int32_t reserved[4];
 } grid_opts;
 
 /* ---- context -------------------------------------------------------------- */
@@ -133,22 +137,26 @@ const char *grid_version(void);
  * inputs read once, outputs written once).  Launches are counted always. */
 typedef struct {
     char name[32];        /* kernel family: bounds, count_scan, tile_search, emit, upsweep_gen,
-                             downsweep_gen, upsweep, downsweep, extract_split, extract, localize */
+                             downsweep_gen, upsweep, downsweep, extract_split, extract, localize,
+                             make_pairs_per_object, cull_emit */
     int64_t launches;
     double total_ms;      /* sum of event-timed durations (0 when profiling is off) */
     double bytes;         /* sum of algorithmic bytes */
 } grid_kernel_stat;
 
 /* Autotuner: builds the given mesh (device pointers, as grid_build) with
- * every candidate configuration - radix digits of 8, 9, 10 and 11 bits,
- * pair generation GRID_PAIRS_FUSED and GRID_PAIRS_EMIT - times each with
- * CUDA events on the context's stream (median of `reps` builds after one
- * warm-up; reps <= 0 means 3) and keeps the fastest for the context's later
- * builds.  Every candidate gives the same grid, so tuning changes speed
- * only.  *chosen (may be NULL) gets the kept radix_bits and pair_gen; times
- * (may be NULL, 8 entries) the median ms of each candidate in the order
- * radix 8..11 x (FUSED, EMIT).  The culling setting is left as it is.
- * Errors as grid_build; on error the context keeps its previous setting. */
+ * every candidate configuration and keeps the fastest for the context's
+ * later builds.  First every radix digit width (8, 9, 10, 11 bits) x pair
+ * generation (GRID_PAIRS_FUSED, GRID_PAIRS_EMIT) with the context's block
+ * shape, then the other block shape (grid_opts.tile_shape) with the best of
+ * those.  Each candidate is timed with CUDA events on the context's stream:
+ * the median of `reps` builds after one warm-up (reps <= 0 means 3).  Every
+ * candidate gives the same grid, so tuning changes speed only.  *chosen
+ * (may be NULL) gets the kept radix_bits, pair_gen and tile_shape; times
+ * (may be NULL, 9 entries) the median ms of each candidate: radix 8..11 x
+ * (FUSED, EMIT), then the other shape.  The culling setting is left as it
+ * is.  Errors as grid_build; on error the context keeps its previous
+ * setting. */
 int grid_ctx_autotune(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
                       float lambda, int32_t reps, grid_opts *chosen, double *times);
 

@@ -119,7 +119,10 @@ class Context:
     PAIR_GEN = {"fused": _lib.GRID_PAIRS_FUSED, "emit": _lib.GRID_PAIRS_EMIT,
                 "per_object": _lib.GRID_PAIRS_PER_OBJECT, "regen": _lib.GRID_PAIRS_REGEN}
 
-    def __init__(self, device: int = 0, radix_bits: int = 0, pair_gen: str = "fused", cull: bool = False):
+    TILE_SHAPE = {"256x12": 0, "384x8": 1}
+
+    def __init__(self, device: int = 0, radix_bits: int = 0, pair_gen: str = "fused", cull: bool = False,
+                 tile_shape: str = "256x12"):
         import torch
         self._torch = torch
         self.device = torch.device("cuda", device)
@@ -128,6 +131,7 @@ class Context:
         opts.radix_bits = int(radix_bits)
         opts.pair_gen = self.PAIR_GEN[pair_gen]
         opts.cull = 1 if cull else 0
+        opts.tile_shape = self.TILE_SHAPE[tile_shape]
         h = ctypes.c_void_p()
         check(self._lib.grid_ctx_create(int(device), ctypes.byref(opts), ctypes.byref(h)), "grid_ctx_create")
         self._h = h
@@ -165,14 +169,16 @@ class Context:
 
     def autotune(self, verts, tris, lam: float, reps: int = 3) -> dict:
         """Times every radix width (8..11) x pair generation (fused, emit) on
-        this mesh and keeps the fastest for later builds (same grid either
-        way).  Returns {"radix_bits", "pair_gen", "times_ms": {(bits, mode): ms}}."""
+        this mesh, then the other radix-kernel block shape with the best of
+        them, and keeps the fastest for later builds (same grid either way).
+        Returns {"radix_bits", "pair_gen", "tile_shape",
+        "times_ms": {(bits, mode): ms, "other_shape": ms}}."""
         torch = self._torch
         v = self._dev(verts, torch.float32, 3)
         t = self._dev(tris, torch.int32, 3)
         self._bind_stream()
         chosen = GridOpts()
-        times = (ctypes.c_double * 8)()
+        times = (ctypes.c_double * 9)()
         check(self._lib.grid_ctx_autotune(self._h, v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], float(lam),
                                           int(reps), ctypes.byref(chosen), times), "grid_ctx_autotune")
         names = {v: k for k, v in self.PAIR_GEN.items()}
@@ -182,7 +188,10 @@ class Context:
             for mode in ("fused", "emit"):
                 tt[(rb, mode)] = float(times[k])
                 k += 1
-        return {"radix_bits": int(chosen.radix_bits), "pair_gen": names[int(chosen.pair_gen)], "times_ms": tt}
+        tt["other_shape"] = float(times[8])
+        shapes = {v: k for k, v in self.TILE_SHAPE.items()}
+        return {"radix_bits": int(chosen.radix_bits), "pair_gen": names[int(chosen.pair_gen)],
+                "tile_shape": shapes[int(chosen.tile_shape)], "times_ms": tt}
 
     def profile(self, enable: bool = True) -> None:
         """Per-kernel CUDA-event timing on (clears the statistics)."""

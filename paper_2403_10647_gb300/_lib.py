@@ -56,7 +56,8 @@ class GridKernelStat(ctypes.Structure):
 
 
 class GridOpts(ctypes.Structure):
-    _fields_ = [("radix_bits", c_int32), ("pair_gen", c_int32), ("cull", c_int32), ("reserved", c_int32 * 5)]
+    _fields_ = [("radix_bits", c_int32), ("pair_gen", c_int32), ("cull", c_int32), ("tile_shape", c_int32),
+                ("reserved", c_int32 * 4)]
 
 
 class GridServeOpts(ctypes.Structure):

@@ -841,8 +841,22 @@ __global__ void wait_selftest_kernel(const unsigned *col, Ctl *ctl, unsigned *ou
     if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = group_lookback(col, 1u, 1u, ctl);
 }
 
+// Resident blocks per SM each radix-kernel shape is compiled for.
+template <int BLOCK>
+__host__ __device__ constexpr int pass_min_blocks()
+{
+    return BLOCK == ALT_BLOCK ? ALT_PASS_MIN_BLOCKS : PASS_MIN_BLOCKS;
+}
+
+template <int BLOCK>
+__host__ __device__ constexpr int gen_min_blocks()
+{
+    return BLOCK == ALT_BLOCK ? ALT_GEN_MIN_BLOCKS : GEN_MIN_BLOCKS;
+}
+
 template <int BLOCK, int ITEMS, int RBITS, int SRC>
-__global__ void __launch_bounds__(BLOCK, SRC == SRC_GEN ? GEN_MIN_BLOCKS : 2048 / BLOCK) upsweep_kernel(UpArgs a)
+__global__ void __launch_bounds__(BLOCK, SRC == SRC_GEN ? gen_min_blocks<BLOCK>() : 2048 / BLOCK)
+    upsweep_kernel(UpArgs a)
 {
     constexpr int T = BLOCK * ITEMS;
     constexpr int R = 1 << RBITS;
@@ -1016,7 +1030,7 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 
 template <int BLOCK, int ITEMS, int RBITS, int IN>
-__global__ void __launch_bounds__(BLOCK, PASS_MIN_BLOCKS) downsweep_kernel(DownArgs a, unsigned gtiles)
+__global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_kernel(DownArgs a, unsigned gtiles)
 {
     constexpr int W = BLOCK / 32;
     constexpr int T = BLOCK * ITEMS;
@@ -1493,29 +1507,29 @@ cudaError_t launch_cull_emit(const CullArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int RBITS, int SRC>
+template <int RBITS, int SRC, int BLOCK>
 static cudaError_t launch_up_t(const UpArgs &a, cudaStream_t s)
 {
-    constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
-    auto k = upsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, SRC>;
+    constexpr int ITEMS = PAIR_TILE / BLOCK;
+    auto k = upsweep_kernel<BLOCK, ITEMS, RBITS, SRC>;
     const size_t smem = sizeof(unsigned) * (3 * (1 << RBITS) + (SRC == SRC_GEN ? padded<PAIR_TILE>() : 0));
     static std::atomic<unsigned long long> configured{0};
     if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
     if (a.gtiles < 1 || a.gtiles > (unsigned)GROUP_TILES) return cudaErrorInvalidValue;
     const unsigned groups = (a.ntiles + a.gtiles - 1) / a.gtiles;
-    k<<<groups, PAIR_BLOCK, smem, s>>>(a);
+    k<<<groups, BLOCK, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int RBITS, int IN>
+template <int RBITS, int IN, int BLOCK>
 static cudaError_t launch_down_t(const DownArgs &a, unsigned ntiles, unsigned gtiles, cudaStream_t s)
 {
-    constexpr int ITEMS = PAIR_TILE / PAIR_BLOCK;
-    auto k = downsweep_kernel<PAIR_BLOCK, ITEMS, RBITS, IN>;
-    constexpr size_t smem = down_smem_bytes<PAIR_BLOCK, ITEMS, RBITS>();
+    constexpr int ITEMS = PAIR_TILE / BLOCK;
+    auto k = downsweep_kernel<BLOCK, ITEMS, RBITS, IN>;
+    constexpr size_t smem = down_smem_bytes<BLOCK, ITEMS, RBITS>();
     static std::atomic<unsigned long long> configured{0};
     if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
-    k<<<ntiles, PAIR_BLOCK, smem, s>>>(a, gtiles);
+    k<<<ntiles, BLOCK, smem, s>>>(a, gtiles);
     return cudaGetLastError();
 }
 
@@ -1526,12 +1540,12 @@ unsigned group_tiles(unsigned ntiles, int nsm)
     return per < 1u ? 1u : (per > (unsigned)GROUP_TILES ? (unsigned)GROUP_TILES : per);
 }
 
-cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s)
+template <int BLOCK>
+static cudaError_t launch_up_b(const UpArgs &a, int rbits, int src, cudaStream_t s)
 {
-    if (a.ntiles == 0) return cudaSuccess;
-#define GG_UP(RB)                                                          \
-    case RB:                                                               \
-        return src == SRC_GEN ? launch_up_t<RB, SRC_GEN>(a, s) : launch_up_t<RB, SRC_MEM>(a, s);
+#define GG_UP(RB)                                                                                   \
+    case RB:                                                                                        \
+        return src == SRC_GEN ? launch_up_t<RB, SRC_GEN, BLOCK>(a, s) : launch_up_t<RB, SRC_MEM, BLOCK>(a, s);
     switch (rbits) {
         GG_UP(8)
         GG_UP(9)
@@ -1543,14 +1557,14 @@ cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s)
 #undef GG_UP
 }
 
-cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, unsigned gtiles, cudaStream_t s)
+template <int BLOCK>
+static cudaError_t launch_down_b(const DownArgs &a, int rbits, int in, unsigned ntiles, unsigned gtiles,
+                                 cudaStream_t s)
 {
-    if (ntiles == 0) return cudaSuccess;
-    if (gtiles < 1 || gtiles > (unsigned)GROUP_TILES) return cudaErrorInvalidValue;
-#define GG_DOWN(RB)                                                        \
-    case RB:                                                               \
-        return in == IN_GEN ? launch_down_t<RB, IN_GEN>(a, ntiles, gtiles, s)  \
-                            : launch_down_t<RB, IN_PAIR>(a, ntiles, gtiles, s);
+#define GG_DOWN(RB)                                                                  \
+    case RB:                                                                         \
+        return in == IN_GEN ? launch_down_t<RB, IN_GEN, BLOCK>(a, ntiles, gtiles, s)  \
+                            : launch_down_t<RB, IN_PAIR, BLOCK>(a, ntiles, gtiles, s);
     switch (rbits) {
         GG_DOWN(8)
         GG_DOWN(9)
@@ -1560,6 +1574,24 @@ cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntil
         return cudaErrorInvalidValue;
     }
 #undef GG_DOWN
+}
+
+cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, int shape, cudaStream_t s)
+{
+    if (a.ntiles == 0) return cudaSuccess;
+    if (shape == SHAPE_MAIN) return launch_up_b<PAIR_BLOCK>(a, rbits, src, s);
+    if (shape == SHAPE_ALT) return launch_up_b<ALT_BLOCK>(a, rbits, src, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, unsigned gtiles, int shape,
+                             cudaStream_t s)
+{
+    if (ntiles == 0) return cudaSuccess;
+    if (gtiles < 1 || gtiles > (unsigned)GROUP_TILES) return cudaErrorInvalidValue;
+    if (shape == SHAPE_MAIN) return launch_down_b<PAIR_BLOCK>(a, rbits, in, ntiles, gtiles, s);
+    if (shape == SHAPE_ALT) return launch_down_b<ALT_BLOCK>(a, rbits, in, ntiles, gtiles, s);
+    return cudaErrorInvalidValue;
 }
 
 unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells)

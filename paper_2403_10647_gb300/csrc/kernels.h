@@ -35,6 +35,15 @@ constexpr int GROUP_TILES = GG_GROUP_TILES;   // most tiles per upsweep block
 // per-tile chain (object marks, records, stores) is latency-bound, so more
 // blocks in flight beat the few registers spilled
 constexpr int GEN_MIN_BLOCKS = GG_GEN_MIN_BLOCKS;
+// Block shapes of the radix-sort kernels, chosen per context (grid_opts
+// tile_shape): PAIR_BLOCK threads x PAIR_TILE / PAIR_BLOCK pairs, or
+// ALT_BLOCK threads with fewer pairs each.  Both cover the same PAIR_TILE
+// pairs per tile, so everything outside these kernels is shared.
+enum { SHAPE_MAIN = 0, SHAPE_ALT = 1 };
+constexpr int ALT_BLOCK = 384;
+static_assert(PAIR_TILE % ALT_BLOCK == 0, "the alternative shape covers whole tiles");
+constexpr int ALT_PASS_MIN_BLOCKS = 3;   // 56 registers, no spill
+constexpr int ALT_GEN_MIN_BLOCKS = 4;
 static_assert(GROUP_TILES * PAIR_TILE <= 65536, "tile offsets inside a group fit 16 bits");
 constexpr int EXTRACT_BLOCK = 256;
 constexpr int EXTRACT_TILE = 4096;
@@ -198,9 +207,10 @@ cudaError_t launch_make_pairs_per_object(const ObjRec *recs, long long n, unsign
 // when there are enough groups to fill the GPU, fewer (down to 1) when the
 // groups would not: a group's tiles are walked by one block in sequence.
 unsigned group_tiles(unsigned ntiles, int nsm);
-cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, cudaStream_t s);
+cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, int shape, cudaStream_t s);
 // gtiles: the tiles per group of the pass's upsweep
-cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, unsigned gtiles, cudaStream_t s);
+cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, unsigned gtiles, int shape,
+                             cudaStream_t s);
 unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells);
 cudaError_t launch_extract_split(const ExtractArgs &a, cudaStream_t s);
 cudaError_t launch_extract(const ExtractArgs &a, cudaStream_t s);

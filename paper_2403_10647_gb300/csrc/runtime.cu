@@ -67,6 +67,7 @@ struct grid_ctx {
     cudaMemPool_t pool = nullptr;
     grid_opts opts{};
     int rbits_max = 9;
+    int shape = 0;               // block shape of the radix kernels (gg::SHAPE_*)
     int pair_gen = GRID_PAIRS_FUSED;
     bool cull = false;
 
@@ -399,7 +400,7 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         {
             KernelScope ks(c, gen_up ? K_UP_GEN : K_UP,
                            gen_up ? 16.0 * nobj + (store ? 8.0 * count : 0.0) : 4.0 * count);
-            GG_CUDA(gg::launch_upsweep(u, sc.rbits, gen_up ? gg::SRC_GEN : gg::SRC_MEM, c->stream));
+            GG_CUDA(gg::launch_upsweep(u, sc.rbits, gen_up ? gg::SRC_GEN : gg::SRC_MEM, c->shape, c->stream));
         }
         gg::DownArgs a{};
         a.keys_in = kin;
@@ -419,7 +420,8 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         a.intra = (const unsigned short *)c->intra.ptr;
         a.ctl = c->d_ctl;
         KernelScope ks(c, gen_down ? K_DOWN_GEN : K_DOWN, gen_down ? 16.0 * nobj + 8.0 * count : 16.0 * count);
-        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_down ? gg::IN_GEN : gg::IN_PAIR, ntiles, gtiles, c->stream));
+        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_down ? gg::IN_GEN : gg::IN_PAIR, ntiles, gtiles, c->shape,
+                                     c->stream));
     }
     return GRID_OK;
 }
@@ -740,6 +742,11 @@ int grid_ctx_create(int device, const grid_opts *opts, grid_ctx **out)
         return GRID_EINVAL;
     }
     c->cull = c->opts.cull == 1;
+    if (c->opts.tile_shape != 0 && c->opts.tile_shape != 1) {
+        delete c;
+        return GRID_EINVAL;
+    }
+    c->shape = c->opts.tile_shape;
     int rc = GRID_OK;
     do {
         if ((rc = cuda_err(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device)))) break;
@@ -866,42 +873,48 @@ int grid_ctx_autotune(grid_ctx *c, const float *verts, int64_t nverts, const int
     if (reps <= 0) reps = 3;
     if (reps > 64) return GRID_EINVAL;
     DeviceGuard g(c->device);
-    const int saved_rbits = c->rbits_max, saved_pg = c->pair_gen;
+    const int saved_rbits = c->rbits_max, saved_pg = c->pair_gen, saved_shape = c->shape;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
         if (e0) cudaEventDestroy(e0);
         return GRID_ECUDA;
     }
+    // median ms of `reps` builds with the context's current setting, after
+    // one warm-up build
+    auto time_setting = [&](double *med) -> int {
+        std::vector<float> ms;
+        for (int r = 0; r <= reps; ++r) {
+            grid_buf cells{}, refs{};
+            cudaEventRecord(e0, c->stream);
+            PoolOut po(&cells, &refs);
+            int rc = build_core(c, verts, nverts, tris, n, lambda, nullptr, po);
+            cudaEventRecord(e1, c->stream);
+            grid_buf_free(c, &cells);
+            grid_buf_free(c, &refs);
+            if (rc != GRID_OK) return rc;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                return GRID_ECUDA;
+            }
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (r > 0) ms.push_back(t);
+        }
+        std::sort(ms.begin(), ms.end());
+        *med = ms[ms.size() / 2];
+        return GRID_OK;
+    };
     const int modes[2] = {GRID_PAIRS_FUSED, GRID_PAIRS_EMIT};
     double best = -1.0;
-    int best_rbits = saved_rbits, best_pg = saved_pg, k = 0, rc = GRID_OK;
+    int best_rbits = saved_rbits, best_pg = saved_pg, best_shape = saved_shape, k = 0, rc = GRID_OK;
+    // digit width x pair generation, with the context's block shape
     for (int rb = 8; rb <= 11 && rc == GRID_OK; ++rb) {
         for (int mi = 0; mi < 2 && rc == GRID_OK; ++mi, ++k) {
             c->rbits_max = rb;
             c->pair_gen = modes[mi];
-            std::vector<float> ms;
-            for (int r = 0; r <= reps && rc == GRID_OK; ++r) {
-                grid_buf cells{}, refs{};
-                cudaEventRecord(e0, c->stream);
-                PoolOut po(&cells, &refs);
-                rc = build_core(c, verts, nverts, tris, n, lambda, nullptr, po);
-                cudaEventRecord(e1, c->stream);
-                grid_buf_free(c, &cells);
-                grid_buf_free(c, &refs);
-                if (rc != GRID_OK) break;
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    cudaGetLastError();
-                    rc = GRID_ECUDA;
-                    break;
-                }
-                float t = 0.0f;
-                cudaEventElapsedTime(&t, e0, e1);
-                if (r > 0) ms.push_back(t);   // the first build of a setting warms it up
-            }
-            if (rc != GRID_OK) break;
-            std::sort(ms.begin(), ms.end());
-            const double med = ms[ms.size() / 2];
+            double med = 0.0;
+            if ((rc = time_setting(&med)) != GRID_OK) break;
             if (times) times[k] = med;
             if (best < 0.0 || med < best) {
                 best = med;
@@ -910,20 +923,38 @@ int grid_ctx_autotune(grid_ctx *c, const float *verts, int64_t nverts, const int
             }
         }
     }
+    // then the other block shape with the winner
+    if (rc == GRID_OK) {
+        c->rbits_max = best_rbits;
+        c->pair_gen = best_pg;
+        c->shape = saved_shape == gg::SHAPE_MAIN ? gg::SHAPE_ALT : gg::SHAPE_MAIN;
+        double med = 0.0;
+        rc = time_setting(&med);
+        if (rc == GRID_OK) {
+            if (times) times[8] = med;
+            if (med < best) {
+                best = med;
+                best_shape = c->shape;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != GRID_OK) {
         c->rbits_max = saved_rbits;
         c->pair_gen = saved_pg;
+        c->shape = saved_shape;
         return rc;
     }
     c->rbits_max = best_rbits;
     c->pair_gen = best_pg;
+    c->shape = best_shape;
     if (chosen) {
         std::memset(chosen, 0, sizeof(*chosen));
         chosen->radix_bits = best_rbits;
         chosen->pair_gen = best_pg;
         chosen->cull = c->cull ? 1 : 0;
+        chosen->tile_shape = best_shape;
     }
     return GRID_OK;
 }

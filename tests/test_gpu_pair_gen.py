@@ -91,6 +91,27 @@ def test_modes_full_size_nonhomogeneous(ctx, mode_ctx, mode):
     assert torch.equal(f.cells, g.cells) and torch.equal(f.refs, g.refs)
 
 
+@pytest.mark.parametrize("radix_bits", [8, 9, 10, 11])
+def test_alt_tile_shape_matches_oracle(radix_bits):
+    """The radix kernels' second block shape (384 threads x 8 pairs per
+    3,072-pair tile) gives the oracle's grid at every digit width, in the
+    fused and the emit pair generation."""
+    import paper_2403_10647_gb300 as pg
+    cases = [scenes.uniform_soup(30_000, seed=411), scenes.nonhomogeneous_soup(25_000, seed=412, extent=30.0),
+             scenes.architectural(50_000, seed=413, size=(40.0, 10.0, 40.0), nblobs=30)]
+    for mode in ("fused", "emit"):
+        c = pg.Context(0, radix_bits=radix_bits, pair_gen=mode, tile_shape="384x8")
+        try:
+            for s in cases:
+                g = c.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+                o = oracle.build_grid(s.verts, s.tris, s.lam)
+                assert g.info.nrefs == o.NO, (radix_bits, mode, s.name)
+                assert np.array_equal(host(g.cells), o.G) and np.array_equal(host(g.refs), o.refs), \
+                    (radix_bits, mode, s.name)
+        finally:
+            c.close()
+
+
 def test_bad_mode_rejected():
     import ctypes
     from paper_2403_10647_gb300 import _lib
@@ -98,6 +119,9 @@ def test_bad_mode_rejected():
     o = _lib.GridOpts()
     o.pair_gen = 7
     h = ctypes.c_void_p()
+    assert lib.grid_ctx_create(0, ctypes.byref(o), ctypes.byref(h)) == _lib.GRID_EINVAL
+    o = _lib.GridOpts()
+    o.tile_shape = 2
     assert lib.grid_ctx_create(0, ctypes.byref(o), ctypes.byref(h)) == _lib.GRID_EINVAL
 
 
@@ -110,8 +134,17 @@ def test_autotune_keeps_a_valid_setting_and_the_same_grid():
         before = c.build(v, t, s.lam)
         r = c.autotune(v, t, s.lam, reps=2)
         assert r["radix_bits"] in (8, 9, 10, 11) and r["pair_gen"] in ("fused", "emit")
-        assert len(r["times_ms"]) == 8 and all(ms > 0 for ms in r["times_ms"].values())
-        assert r["times_ms"][(r["radix_bits"], r["pair_gen"])] == min(r["times_ms"].values())
+        assert r["tile_shape"] in ("256x12", "384x8")
+        tm = r["times_ms"]
+        assert len(tm) == 9 and all(ms > 0 for ms in tm.values())
+        combos = {k: ms for k, ms in tm.items() if k != "other_shape"}
+        # the winning combination was found with the default shape; the other
+        # shape was then tried with it and kept only if faster
+        assert combos[(r["radix_bits"], r["pair_gen"])] == min(combos.values())
+        if r["tile_shape"] == "384x8":
+            assert tm["other_shape"] < combos[(r["radix_bits"], r["pair_gen"])]
+        else:
+            assert tm["other_shape"] >= combos[(r["radix_bits"], r["pair_gen"])]
         after = c.build(v, t, s.lam)
         assert torch.equal(before.cells, after.cells) and torch.equal(before.refs, after.refs)
     finally:
