@@ -64,6 +64,8 @@ struct grid_ctx {
     int nsm = 0;
     cudaStream_t own = nullptr;
     cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;   // grid_build_host: the refs' copy overlaps range extraction
+    cudaEvent_t copy_ev = nullptr;
     cudaMemPool_t pool = nullptr;
     grid_opts opts{};
     int rbits_max = 9;
@@ -454,6 +456,9 @@ int extract_ranges(grid_ctx *c, const unsigned *keys, int64_t count, int64_t nce
 // (ncells + 1) and refs (nrefs).
 struct OutAlloc {
     virtual int alloc(grid_ctx *c, int64_t ncells1, int64_t nrefs, unsigned **cells, unsigned **refs) = 0;
+    // called once the refs are final (their last kernel is enqueued), before
+    // the range steps
+    virtual int refs_ready(grid_ctx *, const unsigned *, int64_t) { return GRID_OK; }
     virtual ~OutAlloc() = default;
 };
 
@@ -585,6 +590,7 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
                                   (unsigned *)c->keys_sorted.ptr, refs));
                 keys = (const unsigned *)c->keys_sorted.ptr;
             }
+            GG_TRY(out.refs_ready(c, refs, kc));
             GG_TRY(extract_ranges(c, keys, kc, I.ncells, cells));
         } else {
             GG_CUDA(cudaMemsetAsync(cells, 0, (size_t)(I.ncells + 1) * sizeof(unsigned), c->stream));
@@ -642,6 +648,7 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
             GG_TRY(sort_pairs(c, sc, count, true, recs, n, tile_obj, (unsigned)I.res[0], (unsigned)I.res[1],
                               gg::MeshTab{}, nullptr, nullptr, keys_sorted, refs));
         }
+        GG_TRY(out.refs_ready(c, refs, count));
         GG_TRY(extract_ranges(c, keys_sorted, count, I.ncells, cells));
     } else {
         GG_CUDA(cudaMemsetAsync(cells, 0, (size_t)(I.ncells + 1) * sizeof(unsigned), c->stream));
@@ -686,6 +693,27 @@ struct ScratchOut : OutAlloc {
         nrefs = nr;
         *cells = (unsigned *)c->out_cells.ptr;
         *refs = (unsigned *)c->out_refs.ptr;
+        return GRID_OK;
+    }
+};
+
+// Outputs in the context's scratch, bound for host buffers: once the refs
+// are final their device-to-host copy starts on the context's copy stream,
+// so it overlaps range extraction on the build stream.
+struct HostOut : ScratchOut {
+    int32_t *h_refs;
+    int64_t refs_cap;
+    bool copied = false;
+    HostOut(int32_t *hr, int64_t cap) : h_refs(hr), refs_cap(cap) {}
+    int refs_ready(grid_ctx *c, const unsigned *refs, int64_t count) override
+    {
+        if (!h_refs || count <= 0 || count > refs_cap) return GRID_OK;   // copied after the build, or ENOSPC
+        if (!c->copy_stream) GG_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        if (!c->copy_ev) GG_CUDA(cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming));
+        GG_CUDA(cudaEventRecord(c->copy_ev, c->stream));
+        GG_CUDA(cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0));
+        copied = true;   // from here on the caller waits for the copy stream, whatever happens
+        GG_CUDA(cudaMemcpyAsync(h_refs, refs, (size_t)count * 4, cudaMemcpyDeviceToHost, c->copy_stream));
         return GRID_OK;
     }
 };
@@ -797,6 +825,11 @@ void grid_ctx_destroy(grid_ctx *c)
         if (c->h_stage) cudaFreeHost(c->h_stage);
         if (c->pool) cudaMemPoolDestroy(c->pool);
         if (c->own) cudaStreamDestroy(c->own);
+        if (c->copy_stream) {
+            cudaStreamSynchronize(c->copy_stream);
+            cudaStreamDestroy(c->copy_stream);
+        }
+        if (c->copy_ev) cudaEventDestroy(c->copy_ev);
     }
     delete c;
 }
@@ -971,19 +1004,29 @@ int grid_build_host(grid_ctx *c, const float *h_verts, int64_t nverts, const int
     GG_TRY(ensure(c, c->in_tris, std::max<size_t>(tb, 16)));
     if (vb) GG_CUDA(cudaMemcpyAsync(c->in_verts.ptr, h_verts, vb, cudaMemcpyHostToDevice, c->stream));
     if (tb) GG_CUDA(cudaMemcpyAsync(c->in_tris.ptr, h_tris, tb, cudaMemcpyHostToDevice, c->stream));
-    ScratchOut so;
+    HostOut so(h_cells ? h_refs : nullptr, refs_cap);
     grid_info I;
-    GG_TRY(build_core(c, (const float *)c->in_verts.ptr, nverts, (const int32_t *)c->in_tris.ptr, n, lambda,
-                      &I, so));
-    if (info) *info = I;
-    if (!h_cells || !h_refs || cells_cap < so.ncells1 || refs_cap < so.nrefs) return GRID_ENOSPC;
-    GG_CUDA(cudaMemcpyAsync(h_cells, c->out_cells.ptr, (size_t)so.ncells1 * 4, cudaMemcpyDeviceToHost,
-                            c->stream));
-    if (so.nrefs)
-        GG_CUDA(cudaMemcpyAsync(h_refs, c->out_refs.ptr, (size_t)so.nrefs * 4, cudaMemcpyDeviceToHost,
-                                c->stream));
-    GG_CUDA(cudaStreamSynchronize(c->stream));
-    return GRID_OK;
+    int rc = build_core(c, (const float *)c->in_verts.ptr, nverts, (const int32_t *)c->in_tris.ptr, n, lambda,
+                        &I, so);
+    if (rc == GRID_OK) {
+        if (info) *info = I;
+        if (!h_cells || !h_refs || cells_cap < so.ncells1 || refs_cap < so.nrefs) {
+            rc = GRID_ENOSPC;
+        } else {
+            rc = cuda_err(cudaMemcpyAsync(h_cells, c->out_cells.ptr, (size_t)so.ncells1 * 4,
+                                          cudaMemcpyDeviceToHost, c->stream));
+            if (rc == GRID_OK && so.nrefs && !so.copied)
+                rc = cuda_err(cudaMemcpyAsync(h_refs, c->out_refs.ptr, (size_t)so.nrefs * 4,
+                                              cudaMemcpyDeviceToHost, c->stream));
+            if (rc == GRID_OK) rc = cuda_err(cudaStreamSynchronize(c->stream));
+        }
+    }
+    // no copy into the caller's memory is left in flight on return
+    if (so.copied) {
+        const int rc2 = cuda_err(cudaStreamSynchronize(c->copy_stream));
+        if (rc == GRID_OK) rc = rc2;
+    }
+    return rc;
 }
 
 int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, grid_buf *out_cells,

@@ -234,6 +234,31 @@ def test_build_host_matches_device(ctx):
     assert np.array_equal(cells2.numpy(), cells.numpy()) and np.array_equal(refs2.numpy(), refs.numpy())
 
 
+def test_build_host_culled_errors_and_small_buffers():
+    """The host-buffer build in the culling mode equals the oracle's culled
+    grid; a refs buffer that is too small is reallocated; a bad index is
+    reported with no copy left running, and the context then builds again."""
+    import paper_2403_10647_gb300 as pg
+    s = scenes.nonhomogeneous_soup(20_000, seed=11, extent=25.0)
+    c = pg.Context(0, cull=True)
+    try:
+        o = oracle.build_grid(s.verts, s.tris, s.lam, cull=True)
+        small = torch.empty(3, dtype=torch.int32).pin_memory()
+        cells, refs, info = c.build_host(s.verts, s.tris, s.lam,
+                                         cells_out=torch.empty(o.G.shape[0], dtype=torch.int32).pin_memory(),
+                                         refs_out=small)
+        assert info.nrefs == o.NO
+        assert np.array_equal(cells.numpy(), o.G) and np.array_equal(refs.numpy(), o.refs)
+        bad = s.tris.copy()
+        bad[5, 2] = s.verts.shape[0] + 9
+        with pytest.raises(pg.GridError):
+            c.build_host(s.verts, bad, s.lam, cells_out=cells, refs_out=refs)
+        cells2, refs2, _ = c.build_host(s.verts, s.tris, s.lam, cells_out=cells.clone(), refs_out=refs.clone())
+        assert np.array_equal(cells2.numpy(), o.G) and np.array_equal(refs2.numpy(), o.refs)
+    finally:
+        c.close()
+
+
 # ---- edge cases -----------------------------------------------------------------------
 
 def _scene(verts, tris, lam):
