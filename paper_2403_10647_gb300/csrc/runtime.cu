@@ -1002,30 +1002,35 @@ int grid_build_host(grid_ctx *c, const float *h_verts, int64_t nverts, const int
     const size_t vb = (size_t)nverts * 3 * sizeof(float), tb = (size_t)n * 3 * sizeof(int32_t);
     GG_TRY(ensure(c, c->in_verts, std::max<size_t>(vb, 16)));
     GG_TRY(ensure(c, c->in_tris, std::max<size_t>(tb, 16)));
-    if (vb) GG_CUDA(cudaMemcpyAsync(c->in_verts.ptr, h_verts, vb, cudaMemcpyHostToDevice, c->stream));
-    if (tb) GG_CUDA(cudaMemcpyAsync(c->in_tris.ptr, h_tris, tb, cudaMemcpyHostToDevice, c->stream));
+    if (!c->copy_stream) GG_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    if (!c->copy_ev) GG_CUDA(cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming));
     HostOut so(h_cells ? h_refs : nullptr, refs_cap);
     grid_info I;
-    int rc = build_core(c, (const float *)c->in_verts.ptr, nverts, (const int32_t *)c->in_tris.ptr, n, lambda,
-                        &I, so);
-    if (rc == GRID_OK) {
+    int rc = [&]() -> int {
+        // the vertices come in on the copy stream while the triangles come
+        // in on the build stream (once the build stream is done with the
+        // input scratch); the build waits for both
+        GG_CUDA(cudaEventRecord(c->copy_ev, c->stream));
+        GG_CUDA(cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0));
+        if (vb) GG_CUDA(cudaMemcpyAsync(c->in_verts.ptr, h_verts, vb, cudaMemcpyHostToDevice, c->copy_stream));
+        if (tb) GG_CUDA(cudaMemcpyAsync(c->in_tris.ptr, h_tris, tb, cudaMemcpyHostToDevice, c->stream));
+        GG_CUDA(cudaEventRecord(c->copy_ev, c->copy_stream));
+        GG_CUDA(cudaStreamWaitEvent(c->stream, c->copy_ev, 0));
+        GG_TRY(build_core(c, (const float *)c->in_verts.ptr, nverts, (const int32_t *)c->in_tris.ptr, n, lambda,
+                          &I, so));
         if (info) *info = I;
-        if (!h_cells || !h_refs || cells_cap < so.ncells1 || refs_cap < so.nrefs) {
-            rc = GRID_ENOSPC;
-        } else {
-            rc = cuda_err(cudaMemcpyAsync(h_cells, c->out_cells.ptr, (size_t)so.ncells1 * 4,
-                                          cudaMemcpyDeviceToHost, c->stream));
-            if (rc == GRID_OK && so.nrefs && !so.copied)
-                rc = cuda_err(cudaMemcpyAsync(h_refs, c->out_refs.ptr, (size_t)so.nrefs * 4,
-                                              cudaMemcpyDeviceToHost, c->stream));
-            if (rc == GRID_OK) rc = cuda_err(cudaStreamSynchronize(c->stream));
-        }
-    }
-    // no copy into the caller's memory is left in flight on return
-    if (so.copied) {
-        const int rc2 = cuda_err(cudaStreamSynchronize(c->copy_stream));
-        if (rc == GRID_OK) rc = rc2;
-    }
+        if (!h_cells || !h_refs || cells_cap < so.ncells1 || refs_cap < so.nrefs) return GRID_ENOSPC;
+        GG_CUDA(cudaMemcpyAsync(h_cells, c->out_cells.ptr, (size_t)so.ncells1 * 4, cudaMemcpyDeviceToHost,
+                                c->stream));
+        if (so.nrefs && !so.copied)
+            GG_CUDA(cudaMemcpyAsync(h_refs, c->out_refs.ptr, (size_t)so.nrefs * 4, cudaMemcpyDeviceToHost,
+                                    c->stream));
+        return GRID_OK;
+    }();
+    // no copy from or into the caller's memory is left in flight on return
+    const int rc1 = cuda_err(cudaStreamSynchronize(c->stream));
+    const int rc2 = cuda_err(cudaStreamSynchronize(c->copy_stream));
+    if (rc == GRID_OK) rc = rc1 != GRID_OK ? rc1 : rc2;
     return rc;
 }
 
