@@ -263,7 +263,7 @@ int grow(Worker *w, size_t bytes)
 
 // Builds one batch of requests on worker w.  On return each request holds its
 // result or error code.
-void run_batch(grid_server *S, Worker *w, const std::vector<Request *> &rs, const std::vector<Mesh> &ms)
+void run_batch(Worker *w, const std::vector<Request *> &rs, const std::vector<Mesh> &ms)
 {
     const int nb = (int)rs.size();
     // jitter: each perturbed request gets its own slice of the vertex buffer
@@ -397,7 +397,7 @@ void worker_main(grid_server *S, Worker *w)
         }
         if (rs.empty()) continue;
         const Clock::time_point t0 = Clock::now();
-        run_batch(S, w, rs, ms);
+        run_batch(w, rs, ms);
         // a build that failed before its first synchronisation may leave the
         // jitter table copies in flight: drain the stream before the pinned
         // tables are reused
