@@ -130,6 +130,26 @@ def test_sort_pairs(ctx, count, key_bits):
     assert np.array_equal(host(Cs), sC) and np.array_equal(host(Os), sO)
 
 
+@pytest.mark.parametrize("n,extent", [(300_000, 63.0), (600_000, 79.4)])
+def test_mid_size_upsweep_groups(ctx, n, extent):
+    """Sorts of ~6k and ~11k tiles, where the upsweep walks groups of a few
+    tiles each (between the one-tile groups of small sorts and the 16-tile
+    groups of large ones) and the last group is partial, in both radix
+    kernel shapes."""
+    import paper_2403_10647_gb300 as pg
+    s = scenes.nonhomogeneous_soup(n, seed=431, extent=extent)
+    o = oracle.build_grid(s.verts, s.tris, s.lam, method="counting")
+    ntiles = (o.NO + 3071) // 3072
+    assert 4000 < ntiles < 20000   # groups of 4 and 12 tiles on 152 SMs, the last one partial
+    alt = pg.Context(0, tile_shape="384x8")
+    try:
+        for c in (ctx, alt):
+            g = c.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+            assert_grid_equal(g, o, f"mid-size {n}")
+    finally:
+        alt.close()
+
+
 @pytest.mark.parametrize("radix_bits", [8, 9, 10, 11])
 def test_radix_widths_agree(radix_bits):
     import paper_2403_10647_gb300 as pg
