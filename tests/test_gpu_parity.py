@@ -291,7 +291,8 @@ def test_empty(ctx):
     assert host(g.cells).tolist() == [0, 0] and g.refs.numel() == 0 and tuple(g.info.res) == (1, 1, 1)
 
 
-@pytest.mark.parametrize("case", ["one_tri", "single_cell", "flat_z", "point", "huge_plus_small", "needle"])
+@pytest.mark.parametrize("case", ["one_tri", "single_cell", "flat_z", "point", "huge_plus_small", "needle",
+                                  "clamped_x", "clamped_xy"])
 def test_degenerate_scenes(ctx, case):
     g = np.random.Generator(np.random.Philox(5))
     if case == "one_tri":
@@ -307,10 +308,20 @@ def test_degenerate_scenes(ctx, case):
     elif case == "huge_plus_small":   # one triangle spans the whole grid
         v = np.concatenate([[[0, 0, 0], [10, 0, 10], [0, 10, 5]], g.random((3000, 3)) * 10])
         s = _scene(v, np.concatenate([[[0, 1, 2]], 3 + g.integers(0, 3000, (1000, 3))]), 8.0)
-    else:  # a long thin diagonal triangle (many false intersections, Sec. 5)
+    elif case == "needle":  # a long thin diagonal triangle (many false intersections, Sec. 5)
         v = np.concatenate([[[0, 0, 0], [20, 20, 20], [20.01, 20, 20]], g.random((3000, 3)) * 20])
         s = _scene(v, np.concatenate([[[0, 1, 2]], 3 + g.integers(0, 3000, (1000, 3))]), 4.0)
+    elif case == "clamped_x":   # a 1-D scene whose resolution rule asks for 160,000 cells: res_x = 65,535
+        x = g.random(6000) * 1000.0
+        v = np.stack([np.concatenate([x, x + 0.05, x + 0.1]), np.full(18000, 0.5), np.full(18000, 0.25)], axis=1)
+        s = _scene(v, np.stack([np.arange(6000), 6000 + np.arange(6000), 12000 + np.arange(6000)], axis=1), 8.0 / 0.3)
+    else:   # a 2-D sheet with one long axis: x clamps at 65,535 cells, y does not
+        x, y = g.random(4000) * 4000.0, g.random(4000) * 2.0
+        v = np.stack([np.concatenate([x, x + 0.2, x]), np.concatenate([y, y, y + 0.1]), np.full(12000, 1.0)], axis=1)
+        s = _scene(v, np.stack([np.arange(4000), 4000 + np.arange(4000), 8000 + np.arange(4000)], axis=1), 2000.0)
     gg, o = build_both(ctx, s)
+    if case.startswith("clamped"):
+        assert gg.info.res[0] == 65535, gg.info.res
     assert_grid_equal(gg, o, case)
 
 
