@@ -1304,15 +1304,27 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
         }
     }
     __syncthreads();
-    // each cell of the block's range: a branch-free lower bound over the
-    // block's keys (every lane takes the same fixed number of steps)
-    for (unsigned k = tid; k < nc; k += BLOCK) {
+    // each thread takes a run of consecutive cells: the first cell's lower
+    // bound is a full branch-free search over the block's keys, each later
+    // one starts from its predecessor's and usually lies within the next
+    // 8 keys (3 steps), else a full search from there
+    const unsigned cpt = (nc + BLOCK - 1) / BLOCK;
+    const unsigned k0 = min(tid * cpt, nc), k1 = min(k0 + cpt, nc);
+    unsigned pos = 0;
+    for (unsigned k = k0; k < k1; ++k) {
         const unsigned c = c0 + k;
-        unsigned pos = 0;
+        if (k != k0 && pos + 8u <= na && s_keys[pos + 7u] >= c) {
 #pragma unroll
-        for (unsigned step = (unsigned)D; step >= 1u; step >>= 1) {   // D, a power of two, bounds na
-            const unsigned q = pos + step;
-            pos = (q <= na && s_keys[q - 1u] < c) ? q : pos;
+            for (unsigned step = 4u; step >= 1u; step >>= 1) {
+                const unsigned q = pos + step;
+                pos = s_keys[q - 1u] < c ? q : pos;
+            }
+        } else {
+#pragma unroll
+            for (unsigned step = (unsigned)D; step >= 1u; step >>= 1) {   // D, a power of two, bounds na
+                const unsigned q = pos + step;
+                pos = (q <= na && s_keys[q - 1u] < c) ? q : pos;
+            }
         }
         s_g[k] = (unsigned)i0 + pos;
     }
