@@ -353,7 +353,12 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
     const bool store = gen && c->pair_gen != GRID_PAIRS_REGEN;
     GG_TRY(ensure(c, c->intra, (size_t)ntiles * R * sizeof(unsigned short)));
     GG_TRY(ensure(c, c->gpref, (size_t)ngroups * R * sizeof(unsigned)));
-    GG_TRY(ensure(c, c->gstatus, (size_t)ngroups * R * sizeof(unsigned)));
+    // every pass gets its own zeroed look-back words: one clear for the sort
+    const size_t status_words = (size_t)ngroups * R;
+    GG_TRY(ensure(c, c->gstatus, (size_t)std::max(sc.passes, 1) * status_words * sizeof(unsigned)));
+    if (sc.passes > 0)
+        GG_CUDA(cudaMemsetAsync(c->gstatus.ptr, 0, (size_t)sc.passes * status_words * sizeof(unsigned),
+                                c->stream));
     if (sc.passes > 1 || store) {
         GG_TRY(ensure(c, c->keys[0], elem));
         GG_TRY(ensure(c, c->vals[0], elem));
@@ -377,7 +382,6 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         const bool first = p == 0;
         const unsigned *kin = first ? keys_in : ko[p - 1];
         const unsigned *vin = first ? vals_in : vo[p - 1];
-        GG_CUDA(cudaMemsetAsync(c->gstatus.ptr, 0, (size_t)ngroups * R * sizeof(unsigned), c->stream));
         gg::UpArgs u{};
         u.keys_in = kin;
         u.recs = recs;
@@ -394,7 +398,7 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         u.bits = sc.bits[p];
         u.intra = (unsigned short *)c->intra.ptr;
         u.gpref = (unsigned *)c->gpref.ptr;
-        u.status = (unsigned *)c->gstatus.ptr;
+        u.status = (unsigned *)c->gstatus.ptr + (size_t)p * status_words;
         u.dbase = c->d_dbase + p * gg::MAX_RADIX;
         u.ctl = c->d_ctl;
         const bool gen_up = first && gen;
