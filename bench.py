@@ -375,7 +375,7 @@ def bench_cull(scene, reps: int = 5):
 
 
 def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 2, max_batch: int = 32, batch_pairs: int = 0,
-                radix_bits: int = 8):
+                radix_bits: int = 8, small_lane: bool = True):
     """The rebuild-serving loop: a pool of registered meshes, requests with
     per-request jitter (sigma 0.01).  (1) open loop: Poisson arrivals at
     `rate` for `seconds`, latency percentiles; (2) saturated: the first 1000
@@ -389,7 +389,8 @@ def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 2, max_batch: 
     pool = scenes.serving_pool()
     arr, mesh, seeds = scenes.poisson_requests(rate, seconds, len(pool))
     sigma = 0.01
-    srv = pg.Server(0, nworkers=nworkers, max_batch=max_batch, batch_pairs=batch_pairs, radix_bits=radix_bits)
+    srv = pg.Server(0, nworkers=nworkers, max_batch=max_batch, batch_pairs=batch_pairs, radix_bits=radix_bits,
+                    small_lane=small_lane)
     try:
         ids = [srv.register(s.verts, s.tris, s.lam) for s in pool]
         # warm every worker and mesh once
@@ -474,6 +475,7 @@ def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 2, max_batch: 
         srv.close()
     return {"pool_meshes": len(pool), "pool_tris": [int(min(s.n for s in pool)), int(max(s.n for s in pool))],
             "sigma": sigma, "workers": nworkers, "max_batch": max_batch, "batch_pairs": batch_pairs or (1 << 24),
+            "small_lane": bool(small_lane),
             "open_loop": open_loop, "saturated": saturated}
 
 

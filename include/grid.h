@@ -353,7 +353,12 @@ typedef struct {
     int64_t hbm_budget;   /* bytes that admitted requests may reserve; 0 -> 3/4 of the device's free
                              memory when the server is created */
     int32_t radix_bits;   /* as grid_opts.radix_bits; 0 -> default */
-    int32_t reserved[5];
+    int32_t arrival_order; /* 0 (default): while every other worker runs a request too large to
+                             batch (estimated pairs above batch_pairs), a free worker takes the
+                             oldest requests that fit a batch first, so they do not queue behind
+                             the large ones; large requests keep their order among themselves and
+                             run as soon as no smaller one waits.  1: strict arrival order */
+    int32_t reserved[4];
 } grid_serve_opts;
 
 typedef struct {

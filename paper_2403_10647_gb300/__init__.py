@@ -429,7 +429,7 @@ class Server:
     become free; admission is by a device-memory budget."""
 
     def __init__(self, device: int = 0, nworkers: int = 0, max_batch: int = 0, batch_pairs: int = 0,
-                 hbm_budget: int = 0, radix_bits: int = 0):
+                 hbm_budget: int = 0, radix_bits: int = 0, small_lane: bool = True):
         import torch
         self._torch = torch
         self.device = torch.device("cuda", device)
@@ -437,6 +437,7 @@ class Server:
         o = GridServeOpts()
         o.nworkers, o.max_batch, o.batch_pairs = int(nworkers), int(max_batch), int(batch_pairs)
         o.hbm_budget, o.radix_bits = int(hbm_budget), int(radix_bits)
+        o.arrival_order = 0 if small_lane else 1   # small lane: small requests pass large ones
         h = ctypes.c_void_p()
         check(self._lib.grid_serve_create(int(device), ctypes.byref(o), ctypes.byref(h)), "grid_serve_create")
         self._h = h

@@ -62,7 +62,7 @@ class GridOpts(ctypes.Structure):
 
 class GridServeOpts(ctypes.Structure):
     _fields_ = [("nworkers", c_int32), ("max_batch", c_int32), ("batch_pairs", c_int64),
-                ("hbm_budget", c_int64), ("radix_bits", c_int32), ("reserved", c_int32 * 5)]
+                ("hbm_budget", c_int64), ("radix_bits", c_int32), ("arrival_order", c_int32), ("reserved", c_int32 * 4)]
 
 
 class GridServeStats(ctypes.Structure):

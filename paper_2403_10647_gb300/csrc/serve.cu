@@ -219,6 +219,7 @@ struct grid_server {
     int64_t budget = 0, reserved = 0, peak_reserved = 0;
     bool stop = false;
     std::vector<std::unique_ptr<Worker>> workers;
+    int busy_large = 0;         // workers running a request above batch_pairs
     std::mutex register_mu;
 
     // statistics since the last reset
@@ -378,24 +379,46 @@ void worker_main(grid_server *S, Worker *w)
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
             if (S->stop) return;
+            auto is_large = [&](uint64_t t) {
+                auto it = S->reqs.find(t);
+                return it != S->reqs.end() && S->meshes[it->second->mesh].est_pairs > S->opts.batch_pairs;
+            };
+            // unless strict arrival order is asked for, the last worker not
+            // busy with a large request passes over large ones while a
+            // smaller one waits
+            bool skip_large = false;
+            if (!S->opts.arrival_order && S->busy_large >= (int)S->workers.size() - 1 && S->workers.size() > 1) {
+                for (uint64_t t : S->queue)
+                    if (!is_large(t)) {
+                        skip_large = true;
+                        break;
+                    }
+            }
             int64_t pairs = 0;
-            while (!S->queue.empty() && (int)rs.size() < S->opts.max_batch) {
-                auto it = S->reqs.find(S->queue.front());
+            for (auto qi = S->queue.begin(); qi != S->queue.end() && (int)rs.size() < S->opts.max_batch;) {
+                auto it = S->reqs.find(*qi);
                 if (it == S->reqs.end()) {   // cannot happen: queued requests are never released
-                    S->queue.pop_front();
+                    qi = S->queue.erase(qi);
                     continue;
                 }
                 Request *r = it->second.get();
                 const Mesh &m = S->meshes[r->mesh];
+                if (skip_large && m.est_pairs > S->opts.batch_pairs) {
+                    ++qi;
+                    continue;
+                }
                 if (!rs.empty() && pairs + m.est_pairs > S->opts.batch_pairs) break;
-                S->queue.pop_front();
+                qi = S->queue.erase(qi);
                 r->state = Q_RUNNING;
                 rs.push_back(r);
                 ms.push_back(m);
                 pairs += m.est_pairs;
             }
+            if (pairs > S->opts.batch_pairs) S->busy_large += 1;   // a single large request
         }
         if (rs.empty()) continue;
+        int64_t batch_est = 0;
+        for (const Mesh &m : ms) batch_est += m.est_pairs;
         const Clock::time_point t0 = Clock::now();
         run_batch(w, rs, ms);
         // a build that failed before its first synchronisation may leave the
@@ -419,6 +442,7 @@ void worker_main(grid_server *S, Worker *w)
             }
             S->batches += 1;
             if (rs.size() > 1) S->batched_requests += (int64_t)rs.size();
+            if (batch_est > S->opts.batch_pairs) S->busy_large -= 1;
             S->t_last = t1;
         }
         S->cv_done.notify_all();
@@ -461,7 +485,7 @@ int grid_serve_create(int device, const grid_serve_opts *opts, grid_server **out
     grid_serve_opts o{};
     if (opts) o = *opts;
     if (o.nworkers < 0 || o.nworkers > 64 || o.max_batch < 0 || o.max_batch > 4096 || o.batch_pairs < 0 ||
-        o.hbm_budget < 0)
+        o.hbm_budget < 0 || (o.arrival_order != 0 && o.arrival_order != 1))
         return GRID_EINVAL;
     if (o.nworkers == 0) o.nworkers = 2;
     if (o.max_batch == 0) o.max_batch = 32;

@@ -179,6 +179,42 @@ def test_batches_form_behind_a_busy_worker(ctx, pool):
         srv.close()
 
 
+def test_small_request_passes_large_ones(ctx, pool):
+    """Two workers, three rebuilds too large to batch and a small request
+    queued behind them: with the default small lane the small request runs
+    before the third large one, which is still unfinished when the small one
+    is done.  (In strict arrival order the third large one starts first; how
+    the two then finish depends on timing, so only the results are checked.)
+    Every result matches the oracle."""
+    import paper_2403_10647_gb300 as pg
+    big = scenes.nonhomogeneous_soup(1_000_000, seed=306)
+    for small_lane in (True, False):
+        srv = pg.Server(0, nworkers=2, small_lane=small_lane)
+        try:
+            bid = srv.register(big.verts, big.tris, big.lam)
+            sid = srv.register(pool[0].verts, pool[0].tris, pool[0].lam)
+            large = [srv.submit(bid, 0.01, 10 + k) for k in range(3)]
+            tk = srv.submit(sid, 0.01, 99)
+            r = srv.wait(tk, timeout=120)
+            p2 = srv.poll(large[2])   # keep the result: dropping it releases the ticket
+            third_done = p2 is not None
+            o = oracle.build_grid(scenes.jitter_vertices(pool[0].verts, 0.01, 99), pool[0].tris, pool[0].lam)
+            assert_same_as_oracle(r, o, "small request")
+            r.release()
+            if small_lane:
+                assert not third_done, "the small request waited for the third large one"
+            for k, t in enumerate(large):
+                rl = p2 if k == 2 and p2 is not None else srv.wait(t, timeout=120)
+                assert rl.info.nrefs > (1 << 24), rl.info.nrefs
+                if k == 2:
+                    ob = oracle.build_grid(scenes.jitter_vertices(big.verts, 0.01, 12), big.tris, big.lam,
+                                           method="counting")
+                    assert_same_as_oracle(rl, ob, "third large request")
+                rl.release()
+        finally:
+            srv.close()
+
+
 def test_admission_refuses_beyond_budget(ctx, pool):
     import paper_2403_10647_gb300 as pg
     sc = pool[4]
