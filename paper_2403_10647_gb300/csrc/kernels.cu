@@ -19,11 +19,19 @@
 //   downsweep_kernel     one stable LSD radix-sort pass (RadixSort of Algorithm
 //                        1): warp multisplit ranking, shared-memory staged,
 //                        coalesced scatter.
-//   extract_kernel       RunLengthEncode + NonEmptyCells + ExclusiveSum fused as
+//   extract_split_kernel, extract_kernel
+//                        RunLengthEncode + NonEmptyCells + ExclusiveSum fused as
 //                        a merge path of the sorted keys against the cell ids.
+//   cull_emit_kernel     culling mode (the triangle/cell test Sec. 6 leaves as
+//                        future work): regenerates each tile's box pairs,
+//                        tests them, compacts the kept ones in object order.
 //   bounds_batched_kernel, localize_kernel
 //                        the same method over a batch of meshes flattened into
 //                        one problem.
+//   wait_selftest_kernel the radix sort's bounded look-back run against a
+//                        predecessor that never publishes (failure detection).
+// The radix kernels are built for two block shapes (256 x 12 and 384 x 8
+// pairs per 3,072-pair tile) and for digits of 8 to 11 bits.
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
