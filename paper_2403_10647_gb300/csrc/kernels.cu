@@ -1268,7 +1268,6 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
     constexpr int D = BLOCK * ITEMS;
     static_assert((D & (D - 1)) == 0, "the lower-bound steps halve from D");
     __shared__ unsigned s_keys[D];
-    __shared__ unsigned s_g[D];
     const int tid = threadIdx.x;
     const unsigned long long nA = a.count, nB = a.ncells + 1ull;
     const unsigned long long M = nA + nB;
@@ -1334,10 +1333,10 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
                 pos = (q <= na && s_keys[q - 1u] < c) ? q : pos;
             }
         }
-        s_g[k] = (unsigned)i0 + pos;
+        // written straight from the thread's run: the runs of neighbouring
+        // lanes are a few cells apart, so a warp's stores share sectors
+        a.G[(unsigned long long)c0 + k] = (unsigned)i0 + pos;
     }
-    __syncthreads();
-    for (unsigned k = tid; k < nc; k += BLOCK) a.G[(unsigned long long)c0 + k] = s_g[k];
 }
 
 // ---------------------------------------------------------------------------
