@@ -112,6 +112,34 @@ def test_alt_tile_shape_matches_oracle(radix_bits):
             c.close()
 
 
+def test_alt_tile_shape_batched_and_culled():
+    """The second radix-kernel shape in a batched build (each mesh equals
+    its own build and the oracle) and in a culled build (equals the
+    oracle's culled grid)."""
+    import paper_2403_10647_gb300 as pg
+    batch = [scenes.uniform_soup(6_000, seed=421), scenes.nonhomogeneous_soup(15_000, seed=422, extent=25.0),
+             scenes.Scene("empty", np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), 4.0),
+             scenes.architectural(30_000, seed=423, size=(30.0, 8.0, 30.0), nblobs=20)]
+    c = pg.Context(0, tile_shape="384x8")
+    try:
+        grids = c.build_batched([(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam) for s in batch])
+        for s, g in zip(batch, grids):
+            o = oracle.build_grid(s.verts, s.tris, s.lam)
+            assert g.info.nrefs == o.NO, s.name
+            assert np.array_equal(host(g.cells), o.G) and np.array_equal(host(g.refs), o.refs), s.name
+    finally:
+        c.close()
+    cc = pg.Context(0, tile_shape="384x8", cull=True)
+    try:
+        s = batch[1]
+        g = cc.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+        o = oracle.build_grid(s.verts, s.tris, s.lam, cull=True)
+        assert g.info.nrefs == o.NO
+        assert np.array_equal(host(g.cells), o.G) and np.array_equal(host(g.refs), o.refs)
+    finally:
+        cc.close()
+
+
 def test_bad_mode_rejected():
     import ctypes
     from paper_2403_10647_gb300 import _lib
