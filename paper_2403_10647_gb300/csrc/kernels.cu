@@ -1037,6 +1037,44 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// One-dimensional bulk copy global -> shared by the TMA engine, completing
+// on a shared-memory mbarrier (transaction bytes).  dst, src and bytes must
+// be multiples of 16.
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst), b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+// Waits for phase 0 of the mbarrier, at most SPIN_LIMIT polls; false if the
+// wait gave up (the caller records ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_phase0(unsigned long long *bar)
+{
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    for (unsigned spins = 0; spins < SPIN_LIMIT; ++spins) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(b)
+                     : "memory");
+        if (done) return true;
+        if (spins > 8) __nanosleep(32);
+    }
+    return false;
+}
+
 template <int BLOCK, int ITEMS, int RBITS, int IN>
 __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_kernel(DownArgs a, unsigned gtiles)
 {
@@ -1057,6 +1095,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_ker
     unsigned *s_dstart = reinterpret_cast<unsigned *>(s_wh + W * R);          // [R]
     unsigned *s_gbase = s_dstart + R;           // [R]
     unsigned *s_tmp = s_gbase + R;              // [W]
+    __shared__ __align__(8) unsigned long long s_vbar;   // the value tile's bulk copy
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned nd = 1u << a.bits;
@@ -1076,6 +1115,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_ker
     // keys of this lane's items in registers, values in shared memory;
     // item i of this lane is element e = w * 32 * ITEMS + i * 32 + lane
     unsigned keys[ITEMS];
+    bool bulk = false;   // values arriving by a bulk copy
     if (IN == IN_GEN) {
         unsigned om[ITEMS], objs[ITEMS];
         zero_marks<BLOCK, ITEMS>(s_mark);
@@ -1095,11 +1135,16 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_ker
         }
         __syncthreads();   // the staging buffer is read out; the masks take it
     } else {
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const unsigned e = w * 32 * ITEMS + i * 32 + lane;
-            if (e < cnt) cp_async4(&s_vin[e], a.vals_in + j0 + e);
+        // the tile's values are one contiguous run: the TMA engine copies
+        // its 16-byte part in one bulk transfer (when the caller's array is
+        // 16-byte aligned), the last few words go by cp.async
+        bulk = (reinterpret_cast<unsigned long long>(a.vals_in) & 15ull) == 0ull && cnt >= 4u;
+        const unsigned nbulk = bulk ? (cnt & ~3u) : 0u;
+        if (bulk && tid == 0) {
+            mbar_init(&s_vbar, 1u);
+            bulk_copy_g2s(s_vin, a.vals_in + j0, nbulk * 4u, &s_vbar);
         }
+        for (unsigned e = nbulk + tid; e < cnt; e += BLOCK) cp_async4(&s_vin[e], a.vals_in + j0 + e);
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const unsigned e = w * 32 * ITEMS + i * 32 + lane;
@@ -1190,7 +1235,10 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_ker
             ex += loc[k];
         }
     }
-    if (IN != IN_GEN) cp_async_wait_all();
+    if (IN != IN_GEN) {
+        cp_async_wait_all();
+        if (bulk && !mbar_wait_phase0(&s_vbar)) atomicOr(&a.ctl->err, ERR_TIMEOUT);
+    }
     __syncthreads();
     // stage the tile in shared memory in locally sorted order
 #pragma unroll
