@@ -109,6 +109,9 @@ def pin_fig1_cells():
         (_tri((3.5, 3.5, 3.5), (4.0, 4.0, 4.0), (3.7, 3.6, 3.6)), (3, 3, 3), (3, 3, 3), 1),
         # a triangle spanning the whole grid
         (_tri((0.0, 0.0, 0.0), (4.0, 0.0, 4.0), (0.0, 4.0, 2.0)), (0, 0, 0), (3, 3, 3), 64),
+        # a point below the grid's origin clamps into the first cell (a
+        # scene's own bounds never produce one; the clamp still fixes it)
+        (_tri((-0.5, 0.5, 0.5), (0.5, -2.0, 0.5), (0.2, 0.6, -0.1)), (0, 0, 0), (0, 0, 0), 1),
     ]
     verts = np.concatenate([c[0] for c in cases]).reshape(-1, 3)
     tris = np.arange(verts.shape[0], dtype=np.int32).reshape(-1, 3)

@@ -8,6 +8,7 @@ import re
 import numpy as np
 import pytest
 
+import _pins
 import oracle
 from paper_2403_10647_gb300 import _lib
 from paper_2403_10647_gb300 import build as pbuild
@@ -74,6 +75,18 @@ def test_plan_matches_oracle_bit_for_bit(lib):
             assert np.array_equal(np.array(info.scale[:], np.float32), p.scale), k
             assert info.ncells == p.ncells
             assert info.key_bits == (p.ncells - 1).bit_length()
+
+
+def test_plan_golden_cases(lib):
+    """The library's host plan on the hand-worked resolution cases (closed
+    forms, FP64 volumes that FP32 would round)."""
+    for row in _pins.read_plan_cases():
+        lo, hi, n, lam = row[0:3], row[3:6], int(row[6]), row[7]
+        rc, info = _plan_c(lib, lo, hi, n, lam)
+        assert rc == 0, row
+        assert tuple(info.res) == tuple(int(r) for r in row[8:11]), (row, tuple(info.res))
+        assert np.array_equal(np.array(info.scale[:], np.float32), np.array(row[11:14], np.float32)), row
+        assert info.ncells == int(row[14]), row
 
 
 def test_plan_errors(lib):

@@ -53,6 +53,16 @@ MUTANTS = {
     "cull_normal_component_swapped": ("ax[0][1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];",
                                       "ax[0][1] = e[0][0] * e[1][2] - e[0][2] * e[1][0];"),
     "cull_no_far_face_clamp": ("q[3 * v + a] = u > (float)res[a] ? (float)res[a] : u;", "q[3 * v + a] = u;"),
+    # plan and mapping
+    "plan_no_res_max_clamp": ("if (r > (double)OR_RES_MAX) r = (double)OR_RES_MAX;", ""),
+    "plan_overflow_unchecked": ("if (nc > INT32_MAX) return OR_EOVERFLOW;", ""),
+    "plan_cbrt_for_two_axes": ("(d == 2) ? sqrt(q)", "(d == 2) ? cbrt(q)"),
+    "plan_volume_in_fp32": ("vol = vol * (double)e[a];", "vol = (double)(float)(vol * (double)e[a]);"),
+    "cell_no_clamp_lo": ("if (f < 0.0f) return 0;", ""),
+    "scan_overflow_unchecked": ("if (s > INT32_MAX) { *total = s; return OR_EOVERFLOW; }", ""),
+    "coords_z_divisor": ("int64_t z = rid / (mx * my);", "int64_t z = rid / (mx * mx);"),
+    "coords_x_term": ("int64_t x = rid - mx * (y + my * z);", "int64_t x = rid - mx * (y + mx * z);"),
+    "inclusive_sum_dropped_term": ("O[j] = O[j] + O[j - 1];", "O[j] = O[j - 1];"),
     "place_reversed": ("for (int64_t j = 0; j < NO; ++j) refs[cnt[C[j]]++] = O[j];",
                        "for (int64_t j = NO - 1; j >= 0; --j) refs[cnt[C[j]]++] = O[j];"),
 }
