@@ -182,9 +182,9 @@ int grid_build(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t 
                int64_t n, float lambda, grid_buf *out_cells, grid_buf *out_refs,
                grid_info *info);
 
-/* The same build from and to HOST memory: copies the inputs to the device,
- * builds, copies cells (int32 [ncells + 1]) and refs (int32 [nrefs]) back
- * into caller buffers of cells_cap / refs_cap elements.  If either is too
+/* The same build (Algorithm 1, Sec. 3) from and to HOST memory: copies the
+ * inputs to the device, builds, copies cells (int32 [ncells + 1]) and refs
+ * (int32 [nrefs]) back into caller buffers of cells_cap / refs_cap elements.  If either is too
  * small the call returns GRID_ENOSPC with info holding the needed sizes.
  * Pinned host memory gives asynchronous copies; pageable memory works too.
  * Returns after the results are in host memory. */
@@ -228,8 +228,10 @@ int grid_build_batched(grid_ctx *ctx, const grid_mesh *meshes, int32_t nmeshes, 
 int grid_bounds(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t *tris,
                 int64_t n, float lo[3], float hi[3]);
 
-/* a1, grid metadata M (host only): resolution, scale and ncells from the
- * bounds and the density rule above; fills info (nrefs = 0, n set).
+/* a1, grid metadata M (host only), the grid description that Algorithm 1
+ * (Sec. 3) takes as given: resolution, scale and ncells from the bounds and
+ * the density rule above (the paper leaves the cell-size rule open, Sec. 6);
+ * fills info (nrefs = 0, n set).
  * GRID_EINVAL for lambda <= 0 or non-finite, GRID_EOVERFLOW if
  * ncells > INT32_MAX. */
 int grid_plan(const float lo[3], const float hi[3], int64_t n, float lambda, grid_info *info);
@@ -416,8 +418,9 @@ int grid_serve_get_stats(grid_server *srv, grid_serve_stats *out, int reset);
 
 /* ---- without allocation -------------------------------------------------- */
 
-/* The range extraction of grid_extract_ranges for callers that cannot
- * allocate device memory when they call it: code running under another
+/* The range extraction of grid_extract_ranges (RunLengthEncode,
+ * NonEmptyCells and ExclusiveSum of Algorithm 1, Sec. 3) for callers that
+ * cannot allocate device memory when they call it: code running under another
  * runtime's memory manager, loops where cudaMalloc / cudaFree would
  * synchronise the device, paths that must not fail for lack of memory once
  * initialised.  The paper has no counterpart; this is a deployment entry
