@@ -184,8 +184,9 @@ int grid_build(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t 
 
 /* The same build (Algorithm 1, Sec. 3) from and to HOST memory: copies the
  * inputs to the device, builds, copies cells (int32 [ncells + 1]) and refs
- * (int32 [nrefs]) back into caller buffers of cells_cap / refs_cap elements.  If either is too
- * small the call returns GRID_ENOSPC with info holding the needed sizes.
+ * (int32 [nrefs]) back into caller buffers of cells_cap / refs_cap
+ * elements.  If either is too small the call returns GRID_ENOSPC with info
+ * holding the needed sizes.
  * Pinned host memory gives asynchronous copies; pageable memory works too.
  * Returns after the results are in host memory. */
 int grid_build_host(grid_ctx *ctx, const float *h_verts, int64_t nverts, const int32_t *h_tris,
