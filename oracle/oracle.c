@@ -49,7 +49,11 @@
 /* ---- boxes: per-triangle AABB and scene bounds (Sec. 3, "boxes") --------- */
 
 /* Validates every vertex index and coordinate the triangles reference and
- * returns the union of the triangle boxes.  n == 0 gives lo = hi = 0. */
+ * returns the union of the triangle boxes.  n == 0 gives lo = hi = 0.
+ * A bound equal to zero is reported as +0.0 whichever sign of zero the
+ * vertices carry (the paper does not distinguish them; -0.0 + 0.0 is +0.0
+ * in round-to-nearest, every other value is unchanged).  The grid does not
+ * depend on the sign: cell coordinates of +-0 offsets are 0 either way. */
 int or_bounds(const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
               float lo[3], float hi[3])
 {
@@ -67,6 +71,10 @@ int or_bounds(const float *verts, int64_t nverts, const int32_t *tris, int64_t n
                 if (p > hi[a]) hi[a] = p;
             }
         }
+    }
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = lo[a] + 0.0f;
+        hi[a] = hi[a] + 0.0f;
     }
     return OR_OK;
 }

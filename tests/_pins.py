@@ -222,6 +222,25 @@ def pin_bounds():
         raise AssertionError("NaN accepted")
 
 
+def pin_bounds_signed_zero():
+    """Zero bounds are reported as +0.0, whatever sign of zero the vertices
+    carry and in whichever order they come: the minimum over {-0.0, +0.0} is
+    a zero, and the reported zero has no sign bit.  Non-zero bounds keep
+    their exact values."""
+    z, nz = np.float32(0.0), np.float32(-0.0)
+    for first, second in ((nz, z), (z, nz), (nz, nz)):
+        verts = np.array([[first, first, 1.0], [second, 2.0, second], [3.0, second, first],
+                          [1.0, 1.0, 1.0], [2.0, 3.0, 4.0], [1.5, 2.5, 0.5]], np.float32)
+        tris = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+        lo, hi = oracle.bounds(verts, tris)
+        assert np.array_equal(lo.view(np.uint32), np.zeros(3, np.uint32)), lo.view(np.uint32)
+        assert np.array_equal(hi, np.array([3.0, 3.0, 4.0], np.float32))
+    # all-negative-zero axis: both bounds are +0.0
+    verts = np.array([[nz, 1.0, 1.0], [nz, 2.0, 3.0], [nz, 4.0, 2.0]], np.float32)
+    lo, hi = oracle.bounds(verts, np.array([[0, 1, 2]], np.int32))
+    assert lo.view(np.uint32)[0] == 0 and hi.view(np.uint32)[0] == 0
+
+
 def pin_bruteforce(nscenes: int = 300, seed: int = 11):
     """Alg. 1 chain == counting placement == brute force on tiny scenes."""
     g = np.random.Generator(np.random.Philox(seed))
@@ -486,8 +505,8 @@ def pin_cull_invariants():
             assert a.NO < 0.5 * full.NO, (a.NO, full.NO)
 
 
-ALL_PINS = [pin_hand_example, pin_fig1_cells, pin_shifted_cells, pin_point_in_cell, pin_plan_cases, pin_plan_errors, pin_bounds,
-            pin_bruteforce, pin_brute_boxes, pin_library_routines, pin_invariants,
+ALL_PINS = [pin_hand_example, pin_fig1_cells, pin_shifted_cells, pin_point_in_cell, pin_plan_cases, pin_plan_errors,
+            pin_bounds, pin_bounds_signed_zero, pin_bruteforce, pin_brute_boxes, pin_library_routines, pin_invariants,
             pin_cull_hand, pin_cull_exact, pin_cull_far_face, pin_cull_invariants]
 
 

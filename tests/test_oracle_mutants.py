@@ -15,6 +15,7 @@ SRC = os.path.join(ROOT, "oracle", "oracle.c")
 
 MUTANTS = {
     "bounds_min_as_max": ("if (p < lo[a]) lo[a] = p;", "if (p > lo[a]) lo[a] = p;"),
+    "bounds_negative_zero_kept": ("        lo[a] = lo[a] + 0.0f;\n", ""),
     "bounds_index_off_by_one": ("(int64_t)vi >= nverts", "(int64_t)vi > nverts"),
     "plan_floor_not_ceil": ("double r = ceil((double)e[a] * k);", "double r = floor((double)e[a] * k);"),
     "plan_sqrt_not_cbrt": ("(d == 3) ? cbrt(q)", "(d == 3) ? sqrt(q)"),
