@@ -245,6 +245,12 @@ int ctl_error(unsigned err)
     return GRID_OK;
 }
 
+// Scene bounds from their ordered-integer reductions.  The reduction ranks
+// -0.0 below +0.0; a zero bound is reported as +0.0 (adding +0.0 clears the
+// sign of a zero and changes no other value).
+float bound_lo(unsigned lo_inv) { return gg::ordered_to_float(~lo_inv) + 0.0f; }
+float bound_hi(unsigned hi_ord) { return gg::ordered_to_float(hi_ord) + 0.0f; }
+
 int read_ctl(grid_ctx *c)
 {
     GG_CUDA(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
@@ -539,8 +545,8 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
     GG_TRY(ctl_error(c->h_ctl->err));
     float lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
-        lo[a] = gg::ordered_to_float(~c->h_ctl->lo_inv[a]);
-        hi[a] = gg::ordered_to_float(c->h_ctl->hi_ord[a]);
+        lo[a] = bound_lo(c->h_ctl->lo_inv[a]);
+        hi[a] = bound_hi(c->h_ctl->hi_ord[a]);
     }
     // a1: M
     GG_TRY(plan(lo, hi, n, lambda, &I));
@@ -1106,8 +1112,8 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
         float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
         if (meshes[m].n > 0) {
             for (int a = 0; a < 3; ++a) {
-                lo[a] = gg::ordered_to_float(~bstate[6 * m + a]);
-                hi[a] = gg::ordered_to_float(bstate[6 * m + 3 + a]);
+                lo[a] = bound_lo(bstate[6 * m + a]);
+                hi[a] = bound_hi(bstate[6 * m + 3 + a]);
             }
         }
         GG_TRY(plan(lo, hi, meshes[m].n, meshes[m].lambda, &infos[m]));
@@ -1292,8 +1298,8 @@ int grid_bounds(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *
     GG_TRY(read_ctl(c));
     GG_TRY(ctl_error(c->h_ctl->err));
     for (int a = 0; a < 3; ++a) {
-        lo[a] = gg::ordered_to_float(~c->h_ctl->lo_inv[a]);
-        hi[a] = gg::ordered_to_float(c->h_ctl->hi_ord[a]);
+        lo[a] = bound_lo(c->h_ctl->lo_inv[a]);
+        hi[a] = bound_hi(c->h_ctl->hi_ord[a]);
     }
     return GRID_OK;
 }

@@ -27,8 +27,9 @@ def assert_grid_equal(g, o, what=""):
     info = g.info
     assert tuple(info.res) == tuple(o.plan.res), (what, info.res, o.plan.res)
     assert np.array_equal(np.array(info.scale, np.float32), o.plan.scale), what
-    assert np.array_equal(np.array(info.lo, np.float32), o.plan.lo), what
-    assert np.array_equal(np.array(info.hi, np.float32), o.plan.hi), what
+    # bit patterns: a -0.0 bound against +0.0 must not pass
+    assert np.array_equal(np.array(info.lo, np.float32).view(np.uint32), o.plan.lo.view(np.uint32)), what
+    assert np.array_equal(np.array(info.hi, np.float32).view(np.uint32), o.plan.hi.view(np.uint32)), what
     assert info.ncells == o.plan.ncells and info.nrefs == o.NO, (what, info.ncells, info.nrefs, o.NO)
     G, refs = host(g.cells), host(g.refs)
     assert G.shape == o.G.shape and refs.shape == o.refs.shape, what
@@ -291,11 +292,25 @@ def test_empty(ctx):
     assert host(g.cells).tolist() == [0, 0] and g.refs.numel() == 0 and tuple(g.info.res) == (1, 1, 1)
 
 
+def _signed_zero_scene(g, negative: bool):
+    """Random triangles whose min faces (max faces if negative) hold both
+    -0.0 and +0.0, in a random order of the two zeros."""
+    v = g.random((3000, 3)).astype(np.float32)
+    if negative:
+        v = -v
+    tris = g.integers(0, 3000, (1000, 3))
+    for k in range(60):   # 20 zeros per axis on referenced vertices, signs alternating by a coin
+        v[tris[k, 0], k % 3] = np.float32(-0.0) if g.random() < 0.5 else np.float32(0.0)
+    return _scene(v, tris, 4.0)
+
+
 @pytest.mark.parametrize("case", ["one_tri", "single_cell", "flat_z", "point", "huge_plus_small", "needle",
-                                  "clamped_x", "clamped_xy"])
+                                  "clamped_x", "clamped_xy", "signed_zero_min", "signed_zero_max"])
 def test_degenerate_scenes(ctx, case):
     g = np.random.Generator(np.random.Philox(5))
-    if case == "one_tri":
+    if case.startswith("signed_zero"):
+        s = _signed_zero_scene(g, case.endswith("max"))
+    elif case == "one_tri":
         s = _scene([[0, 0, 0], [1, 0.5, 0.2], [0.3, 1, 0.9]], [[0, 1, 2]], 64.0)
     elif case == "single_cell":   # lambda * n / volume < 1: one cell, no sort passes
         s = _scene(g.random((30, 3)), g.integers(0, 30, (10, 3)), 0.05)
@@ -320,6 +335,9 @@ def test_degenerate_scenes(ctx, case):
         v = np.stack([np.concatenate([x, x + 0.2, x]), np.concatenate([y, y, y + 0.1]), np.full(12000, 1.0)], axis=1)
         s = _scene(v, np.stack([np.arange(4000), 4000 + np.arange(4000), 8000 + np.arange(4000)], axis=1), 2000.0)
     gg, o = build_both(ctx, s)
+    if case.startswith("signed_zero"):   # the zero bounds are +0.0 on both sides (compared by bits below)
+        zb = gg.info.hi if case.endswith("max") else gg.info.lo
+        assert all(np.float32(x).view(np.uint32) == 0 for x in zb), zb
     if case.startswith("clamped"):
         assert gg.info.res[0] == 65535, gg.info.res
     assert_grid_equal(gg, o, case)
@@ -440,6 +458,16 @@ def test_batched_matches_oracle_and_plain(ctx):
         if s.n:
             p = ctx.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
             assert torch.equal(p.cells, g.cells) and torch.equal(p.refs, g.refs), s.name
+
+
+def test_batched_signed_zero_bounds(ctx):
+    """Per-mesh bounds of a batch report zero bounds as +0.0, as plain builds
+    and the oracle do (bit patterns compared)."""
+    g = np.random.Generator(np.random.Philox(21))
+    batch = [_signed_zero_scene(g, False), scenes.uniform_soup(2000, seed=3), _signed_zero_scene(g, True)]
+    grids = ctx.build_batched([(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam) for s in batch])
+    for s, gr in zip(batch, grids):
+        assert_grid_equal(gr, oracle.build_grid(s.verts, s.tris, s.lam, method="alg1"), f"batched {s.name}")
 
 
 def test_batched_twice_same_result(ctx):
