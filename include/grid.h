@@ -331,9 +331,10 @@ int grid_jitter(grid_ctx *ctx, const float *verts, float *out, int64_t nverts, f
 /* ---- rebuild-serving loop --------------------------------------------------- */
 
 /* A server keeps registered meshes resident on one GPU and rebuilds them on
- * request: each request names a mesh, a jitter sigma and a seed; the server
- * jitters the mesh's vertices on the device (grid_jitter's definition) and
- * builds its grid with Algorithm 1.  Worker threads, each with its own
+ * request: each request names a mesh and may carry the mesh's new vertex
+ * positions, a jitter sigma and a seed; the server takes the new vertices
+ * (or the registered ones), jitters them on the device if sigma > 0
+ * (grid_jitter's definition) and builds their grid with Algorithm 1.  Worker threads, each with its own
  * stream and context, take queued requests in arrival order; a free worker
  * takes every queued request up to max_batch (and up to batch_pairs estimated
  * pairs) and builds them as one batch (grid_build_batched; grid_build for a
@@ -393,12 +394,26 @@ void grid_serve_destroy(grid_server *srv);
  * grid_build.  Synchronous; safe to call while requests run. */
 int grid_serve_register(grid_server *srv, const float *verts, int64_t nverts, const int32_t *tris,
                         int64_t n, float lambda, int32_t *mesh_id);
-/* Queues a rebuild of mesh_id with jitter sigma (>= 0; 0 = the registered
- * vertices) and seed; *ticket identifies it.  GRID_EAGAIN when admission
- * refuses for now (nothing queued), GRID_ELIMIT when the request's estimate
- * alone exceeds the budget (it can never be admitted), GRID_EINVAL for an
- * unknown mesh or bad sigma. */
-int grid_serve_submit(grid_server *srv, int32_t mesh_id, float sigma, uint64_t seed, uint64_t *ticket);
+/* Queues a rebuild of mesh_id; *ticket identifies it.  The paper's case for
+ * the parallel construction is rebuilding a deforming scene's grid at
+ * interactive rates (Abstract; Sec. 6): new_verts carries the mesh's new
+ * vertex positions as they arrive, float32 [nverts][3] with the registered
+ * mesh's nverts and triangle indices, in host memory (pageable or pinned) or
+ * device memory of the server's device; NULL rebuilds the registered
+ * vertices.  The update is copied into server-owned device memory before the
+ * call returns (the caller may reuse or free its buffer at once; a device
+ * buffer must already hold its values, as the copy does not wait on the
+ * caller's streams), and the request's latency includes that copy.  It
+ * applies to this request only; the registered vertices stay as they are.
+ * sigma (>= 0) and seed add grid_jitter's perturbation on top of the
+ * request's vertices (sigma 0: none).  Admission counts the update's copy
+ * (12 * nverts bytes) besides the rebuild's estimate.  GRID_EAGAIN when
+ * admission refuses for now (nothing queued), GRID_ELIMIT when the request's
+ * estimate alone exceeds the budget (it can never be admitted), GRID_EINVAL
+ * for an unknown mesh or bad sigma, GRID_ENOMEM / GRID_ECUDA if the update
+ * cannot be copied (nothing queued). */
+int grid_serve_submit(grid_server *srv, int32_t mesh_id, const float *new_verts, float sigma, uint64_t seed,
+                      uint64_t *ticket);
 /* If the request has finished: GRID_OK with views of its result (device
  * pointers owned by the server, valid until grid_serve_release; never pass
  * them to grid_buf_free) or the build's error code.  GRID_ENOTREADY while it
@@ -406,7 +421,8 @@ int grid_serve_submit(grid_server *srv, int32_t mesh_id, float sigma, uint64_t s
  * output pointer may be NULL. */
 int grid_serve_poll(grid_server *srv, uint64_t ticket, grid_buf *cells, grid_buf *refs, grid_info *info);
 /* As grid_serve_poll, waiting up to timeout_us (< 0: no limit) for the
- * request to finish; GRID_ETIMEOUT if it has not. */
+ * request to finish; GRID_ETIMEOUT if it has not, GRID_EINVAL if another
+ * thread released the ticket while this one waited. */
 int grid_serve_wait(grid_server *srv, uint64_t ticket, int64_t timeout_us, grid_buf *cells, grid_buf *refs,
                     grid_info *info);
 /* Frees a finished request's result and its admission reservation.
@@ -419,23 +435,26 @@ int grid_serve_get_stats(grid_server *srv, grid_serve_stats *out, int reset);
 
 /* ---- without allocation -------------------------------------------------- */
 
-/* The range extraction of grid_extract_ranges (RunLengthEncode,
- * NonEmptyCells and ExclusiveSum of Algorithm 1, Sec. 3) for callers that
- * cannot allocate device memory when they call it: code running under another
- * runtime's memory manager, loops where cudaMalloc / cudaFree would
- * synchronise the device, paths that must not fail for lack of memory once
- * initialised.  The paper has no counterpart; this is a deployment entry
- * point.  It needs no context and allocates nothing: its scratch (a merge-path
- * split table of 2^18 + 1 words, 1 MiB, and an error word) is a fixed-size
- * device array of the library that every GPU which loads the library keeps
- * until the process exits.
+/* The same cell ranges as grid_extract_ranges, for callers that cannot
+ * allocate device memory when they call it: code running under another
+ * runtime's memory manager (which owns the device budget and forbids foreign
+ * allocations), loops where cudaMalloc / cudaFree would synchronise the
+ * device, paths that must not fail for lack of memory once initialised.  The
+ * paper has no counterpart; this is a deployment entry point.  It needs no
+ * context and allocates nothing: its scratch (a merge-path split table of
+ * 2^18 + 1 words, 1 MiB, and an error word) is a fixed-size device array of
+ * the library that every GPU which loads the library keeps until the process
+ * exits.
  *
  * C_sorted (int32 [count], cell ids sorted ascending, each < ncells) and
  * cells (int32 [ncells + 1]) are device pointers on the calling thread's
  * current device; the work runs on `stream` (a cudaStream_t; NULL = the
  * legacy default stream) and the call returns after it has finished.  The
- * first call on a device looks up the scratch's device address; make that
- * first call before any stream capture.  All calls share the one scratch
+ * first call on a device looks up the scratch's device address and keeps it
+ * for the life of the process; make that first call before any stream
+ * capture, and make no call on a device after cudaDeviceReset has torn down
+ * its context in this process (the kept address would be stale).  The error
+ * word is cleared at the start of every call.  All calls share the one scratch
  * array, which keeps the last call's contents: calls that overlap on the GPU
  * (different streams or threads at the same time) race and must be
  * serialised by the caller.

@@ -12,6 +12,8 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 
+import numpy as np
+
 from . import _lib
 from ._lib import GridError, GridInfo, GridBuf, GridOpts, GridServeOpts, GridServeStats, check
 
@@ -441,6 +443,7 @@ class Server:
         h = ctypes.c_void_p()
         check(self._lib.grid_serve_create(int(device), ctypes.byref(o), ctypes.byref(h)), "grid_serve_create")
         self._h = h
+        self._nverts = {}   # mesh id -> registered vertex count (the size a vertex update must have)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -463,13 +466,32 @@ class Server:
         check(self._lib.grid_serve_register(self._h, v.data_ptr() if v.numel() else None, v.shape[0],
                                             t.data_ptr() if t.numel() else None, t.shape[0], float(lam),
                                             ctypes.byref(mid)), "grid_serve_register")
+        self._nverts[int(mid.value)] = int(v.shape[0])
         return int(mid.value)
 
-    def submit(self, mesh_id: int, sigma: float = 0.0, seed: int = 0):
-        """Queues a rebuild; returns its ticket, or None when admission refuses."""
+    def submit(self, mesh_id: int, sigma: float = 0.0, seed: int = 0, verts=None):
+        """Queues a rebuild; returns its ticket, or None when admission refuses.
+        verts: the mesh's new vertex positions for this request (float32
+        [nverts, 3]; a numpy array or a host or CUDA tensor), copied before
+        the call returns; None rebuilds the registered vertices.  sigma and
+        seed jitter the request's vertices on the device (sigma 0: none)."""
         tk = ctypes.c_uint64()
-        rc = self._lib.grid_serve_submit(self._h, int(mesh_id), float(sigma), int(seed) & 0xFFFFFFFFFFFFFFFF,
+        keep = None
+        ptr = None
+        if verts is not None:
+            torch = self._torch
+            keep = verts if isinstance(verts, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(verts))
+            if keep.dtype != torch.float32 or not keep.is_contiguous() or keep.dim() != 2 or keep.shape[1] != 3:
+                raise ValueError("verts must be a contiguous float32 [nverts, 3] array")
+            nv = self._nverts.get(int(mesh_id))   # unknown ids are left to the C call (GRID_EINVAL)
+            if nv is not None and keep.shape[0] != nv:
+                raise ValueError("verts must have the registered mesh's vertex count")
+            if keep.is_cuda:   # the server's copy does not wait on torch's streams
+                torch.cuda.current_stream(keep.device).synchronize()
+            ptr = keep.data_ptr() if keep.numel() else None
+        rc = self._lib.grid_serve_submit(self._h, int(mesh_id), ptr, float(sigma), int(seed) & 0xFFFFFFFFFFFFFFFF,
                                          ctypes.byref(tk))
+        del keep
         if rc == _lib.GRID_EAGAIN:
             return None
         check(rc, "grid_serve_submit")

@@ -110,7 +110,7 @@ SIGNATURES = {
     "grid_serve_create": (c_int32, [ctypes.c_int, P(GridServeOpts), P(c_void_p)]),
     "grid_serve_destroy": (None, [c_void_p]),
     "grid_serve_register": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_float, P(c_int32)]),
-    "grid_serve_submit": (c_int32, [c_void_p, c_int32, c_float, ctypes.c_uint64, P(ctypes.c_uint64)]),
+    "grid_serve_submit": (c_int32, [c_void_p, c_int32, c_void_p, c_float, ctypes.c_uint64, P(ctypes.c_uint64)]),
     "grid_serve_poll": (c_int32, [c_void_p, ctypes.c_uint64, P(GridBuf), P(GridBuf), P(GridInfo)]),
     "grid_serve_wait": (c_int32, [c_void_p, ctypes.c_uint64, c_int64, P(GridBuf), P(GridBuf), P(GridInfo)]),
     "grid_serve_release": (c_int32, [c_void_p, ctypes.c_uint64]),

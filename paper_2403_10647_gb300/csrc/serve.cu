@@ -70,6 +70,8 @@ struct Request {
     int32_t mesh = 0;
     float sigma = 0.0f;
     uint64_t seed = 0;
+    float *uverts = nullptr;    // the caller's vertex update (server-owned device copy), or null
+    size_t ubytes = 0;
     int64_t est_bytes = 0;
     Clock::time_point t_submit{};
     ReqState state = Q_QUEUED;
@@ -221,6 +223,11 @@ struct grid_server {
     std::vector<std::unique_ptr<Worker>> workers;
     int busy_large = 0;         // workers running a request above batch_pairs
     std::mutex register_mu;
+    // vertex updates: copied at submission into blocks of a server-owned
+    // pool on a stream of their own, freed once their request is built
+    std::mutex upload_mu;
+    cudaStream_t upload = nullptr;
+    cudaMemPool_t upool = nullptr;
 
     // statistics since the last reset
     int64_t submitted = 0, completed = 0, failed = 0, refused = 0, batches = 0, batched_requests = 0;
@@ -271,7 +278,9 @@ void run_batch(Worker *w, const std::vector<Request *> &rs, const std::vector<Me
     std::vector<const float *> vsrc(nb);
     size_t need = 0;
     for (int k = 0; k < nb; ++k) {
-        vsrc[k] = ms[k].verts;
+        // the caller's update if the request carries one, else the
+        // registered vertices; jitter (sigma > 0) perturbs that source
+        vsrc[k] = rs[k]->uverts ? rs[k]->uverts : ms[k].verts;
         if (rs[k]->sigma > 0.0f && ms[k].nverts > 0) need += align256((size_t)ms[k].nverts * 12);
     }
     int rc = GRID_OK;
@@ -287,7 +296,7 @@ void run_batch(Worker *w, const std::vector<Request *> &rs, const std::vector<Me
                 off += align256((size_t)ms[k].nverts * 12);
                 gg::JitterDesc &d = w->h_desc[nj];
                 d = gg::JitterDesc{};
-                d.src = ms[k].verts;
+                d.src = vsrc[k];
                 d.dst = dst;
                 d.seed = rs[k]->seed;
                 d.s = rs[k]->sigma * 1.7320508075688772f;
@@ -429,6 +438,11 @@ void worker_main(grid_server *S, Worker *w)
             for (Request *r : rs)
                 if (r->rc == GRID_OK) r->rc = GRID_ECUDA;
         }
+        // the builds that read the vertex updates have finished
+        for (Request *r : rs) {
+            if (r->uverts) cudaFreeAsync(r->uverts, w->stream);
+            r->uverts = nullptr;
+        }
         const Clock::time_point t1 = Clock::now();
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -505,6 +519,16 @@ int grid_serve_create(int device, const grid_serve_opts *opts, grid_server **out
     } else {
         S->budget = o.hbm_budget;
     }
+    if (rc == GRID_OK) rc = cuda_rc(cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking));
+    if (rc == GRID_OK) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        rc = cuda_rc(cudaMemPoolCreate(&S->upool, &props));
+        uint64_t thr = UINT64_MAX;   // keep freed blocks for the next updates
+        if (rc == GRID_OK) rc = cuda_rc(cudaMemPoolSetAttribute(S->upool, cudaMemPoolAttrReleaseThreshold, &thr));
+    }
     for (int i = 0; rc == GRID_OK && i < o.nworkers; ++i) {
         auto w = std::make_unique<Worker>();
         grid_opts go{};
@@ -546,9 +570,16 @@ void grid_serve_destroy(grid_server *S)
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(S->device);
+    for (auto &kv : S->reqs)   // updates of requests that never ran
+        if (kv.second->uverts) cudaFreeAsync(kv.second->uverts, S->upload);
     S->reqs.clear();   // results free their buffers through the workers' contexts
     for (auto &w : S->workers) destroy_worker(w.get());
     S->workers.clear();
+    if (S->upload) {
+        cudaStreamSynchronize(S->upload);
+        cudaStreamDestroy(S->upload);
+    }
+    if (S->upool) cudaMemPoolDestroy(S->upool);
     for (Mesh &m : S->meshes) {
         if (m.verts) cudaFree(m.verts);
         if (m.tris) cudaFree(m.tris);
@@ -618,31 +649,68 @@ int grid_serve_register(grid_server *S, const float *verts, int64_t nverts, cons
     return rc;
 }
 
-int grid_serve_submit(grid_server *S, int32_t mesh_id, float sigma, uint64_t seed, uint64_t *ticket)
+int grid_serve_submit(grid_server *S, int32_t mesh_id, const float *new_verts, float sigma, uint64_t seed,
+                      uint64_t *ticket)
 {
     if (!S || !ticket || !std::isfinite(sigma) || sigma < 0.0f) return GRID_EINVAL;
+    const Clock::time_point t_submit = Clock::now();   // the update's copy counts in the latency
+    int64_t est = 0, nverts = 0;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (mesh_id < 0 || (size_t)mesh_id >= S->meshes.size()) return GRID_EINVAL;
-        const int64_t est = S->meshes[mesh_id].est_bytes;
+        nverts = S->meshes[mesh_id].nverts;
+        est = S->meshes[mesh_id].est_bytes + (new_verts && nverts > 0 ? (int64_t)align256((size_t)nverts * 12) : 0);
         if (est > S->budget) return GRID_ELIMIT;   // would not fit even with nothing else admitted
         if (S->reserved + est > S->budget) {
             S->refused += 1;
             return GRID_EAGAIN;
         }
-        auto r = std::make_unique<Request>();
+        S->reserved += est;   // held from here, so concurrent submissions see it
+        S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+    }
+    auto r = std::make_unique<Request>();
+    if (new_verts && nverts > 0) {
+        // copy the update now: the caller may reuse its buffer once this returns
+        r->ubytes = (size_t)nverts * 12;
+        int rc = GRID_OK;
+        {
+            std::lock_guard<std::mutex> up(S->upload_mu);
+            int prev = -1;
+            cudaGetDevice(&prev);
+            cudaSetDevice(S->device);
+            void *p = nullptr;
+            rc = cuda_rc(cudaMallocFromPoolAsync(&p, r->ubytes, S->upool, S->upload));
+            if (rc == GRID_OK) {
+                r->uverts = (float *)p;
+                rc = cuda_rc(cudaMemcpyAsync(r->uverts, new_verts, r->ubytes, cudaMemcpyDefault, S->upload));
+                const int rc2 = cuda_rc(cudaStreamSynchronize(S->upload));
+                if (rc == GRID_OK) rc = rc2;
+                if (rc != GRID_OK) {
+                    cudaFreeAsync(r->uverts, S->upload);
+                    cudaStreamSynchronize(S->upload);
+                    r->uverts = nullptr;
+                }
+            }
+            if (prev >= 0) cudaSetDevice(prev);
+        }
+        if (rc != GRID_OK) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->reserved -= est;
+            return rc;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
         r->ticket = S->next_ticket++;
         r->mesh = mesh_id;
         r->sigma = sigma;
         r->seed = seed;
         r->est_bytes = est;
-        r->t_submit = Clock::now();
+        r->t_submit = t_submit;
         if (!S->have_first) {
             S->have_first = true;
             S->t_first = r->t_submit;
         }
-        S->reserved += est;
-        S->peak_reserved = std::max(S->peak_reserved, S->reserved);
         S->submitted += 1;
         *ticket = r->ticket;
         S->queue.push_back(r->ticket);
@@ -670,17 +738,24 @@ int grid_serve_wait(grid_server *S, uint64_t ticket, int64_t timeout_us, grid_bu
 {
     if (!S) return GRID_EINVAL;
     std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->reqs.find(ticket);
-    if (it == S->reqs.end()) return GRID_EINVAL;
-    const Request *r = it->second.get();   // stays valid: only a finished request can be released
-    auto done = [&] { return r->state == Q_DONE; };
+    if (S->reqs.find(ticket) == S->reqs.end()) return GRID_EINVAL;
+    // The request is looked up again on every wake-up, never held across the
+    // wait: another thread may release the ticket between the request
+    // finishing and this thread taking the lock back.
+    auto done = [&] {
+        auto it = S->reqs.find(ticket);
+        return it == S->reqs.end() || it->second->state == Q_DONE;
+    };
     if (timeout_us < 0) {
         S->cv_done.wait(lk, done);
     } else if (!S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done)) {
         return GRID_ETIMEOUT;
     }
-    if (r->rc != GRID_OK) return r->rc;
-    fill_result(*r, cells, refs, info);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return GRID_EINVAL;   // released by another thread meanwhile
+    const Request &r = *it->second;
+    if (r.rc != GRID_OK) return r.rc;
+    fill_result(r, cells, refs, info);
     return GRID_OK;
 }
 

@@ -347,3 +347,151 @@ def test_latency_statistics(ctx, pool):
         assert srv.stats()["completed"] == 0   # reset cleared the counters
     finally:
         srv.close()
+
+
+# ---- caller-supplied vertex updates -------------------------------------------------
+
+def _deformed(sc, k):
+    """New vertex positions for mesh sc, the k-th frame of a deformation: a
+    shear and a swell that move the bounds and the cells of the triangles."""
+    v = sc.verts.astype(np.float64)
+    c = v.mean(axis=0)
+    out = v + (0.02 + 0.01 * k) * np.stack([v[:, 1] - c[1], np.sin(v[:, 0]), 0.5 * (v[:, 2] - c[2])], axis=1)
+    return np.ascontiguousarray(out.astype(np.float32))
+
+
+def _update_oracle(sc, verts, sigma, seed):
+    v = scenes.jitter_vertices(verts, sigma, seed) if sigma > 0 else verts
+    return oracle.build_grid(v, sc.tris, sc.lam, method="alg1" if sc.n < 50_000 else "counting")
+
+
+def test_vertex_updates_match_oracle(ctx, pool):
+    """Requests carrying new vertex positions (from host memory and from
+    device memory, with and without jitter on top) are built from those
+    positions; the registered vertices stay as they were."""
+    import paper_2403_10647_gb300 as pg
+    srv = pg.Server(0, nworkers=2, max_batch=4)
+    try:
+        ids = [srv.register(s.verts, s.tris, s.lam) for s in pool]
+        cases = []   # (mesh, update or None, where, sigma, seed)
+        for m, sc in enumerate(pool):
+            cases.append((m, _deformed(sc, 1), "host", 0.0, 0))
+            cases.append((m, _deformed(sc, 2), "cuda", 0.0, 0))
+            cases.append((m, _deformed(sc, 3), "host", 0.01, 1000 + m))
+            cases.append((m, None, "", 0.0, 0))
+        tickets = []
+        for m, upd, where, s, sd in cases:
+            verts = None if upd is None else (dev(upd, torch.float32) if where == "cuda" else upd)
+            tickets.append(srv.submit(ids[m], s, sd, verts=verts))
+        for (m, upd, where, s, sd), tk in zip(cases, tickets):
+            r = srv.wait(tk, timeout=120)
+            sc = pool[m]
+            assert_same_as_oracle(r, _update_oracle(sc, sc.verts if upd is None else upd, s, sd),
+                                  f"mesh {m} update {where or 'none'} sigma {s}")
+            r.release()
+        st = srv.stats()
+        assert st["completed"] == len(cases) and st["failed"] == 0 and st["reserved_bytes"] == 0
+    finally:
+        srv.close()
+
+
+def test_vertex_update_buffer_is_copied_at_submission(ctx, pool):
+    """The caller may overwrite its buffer as soon as submit returns: the
+    request keeps the positions it was submitted with."""
+    import paper_2403_10647_gb300 as pg
+    sc = pool[1]
+    srv = pg.Server(0, nworkers=1)
+    try:
+        mid = srv.register(sc.verts, sc.tris, sc.lam)
+        frames = [_deformed(sc, k) for k in range(4)]
+        host_buf = frames[0].copy()
+        dev_buf = dev(frames[0], torch.float32)
+        tks = []
+        for k in range(4):   # one reused host buffer and one reused device buffer, overwritten each frame
+            host_buf[:] = frames[k]
+            tks.append(srv.submit(mid, 0.0, 0, verts=host_buf))
+            dev_buf.copy_(torch.from_numpy(frames[(k + 1) % 4]).cuda())
+            tks.append(srv.submit(mid, 0.0, 0, verts=dev_buf))
+        host_buf[:] = 0.0
+        dev_buf.zero_()
+        for k in range(4):
+            for j, f in enumerate((frames[k], frames[(k + 1) % 4])):
+                r = srv.wait(tks[2 * k + j], timeout=120)
+                assert_same_as_oracle(r, _update_oracle(sc, f, 0.0, 0), f"frame {k} buffer {j}")
+                r.release()
+    finally:
+        srv.close()
+
+
+def test_vertex_updates_alone_equals_in_mix(ctx, pool):
+    """Requests with vertex updates give the same result alone (one worker,
+    batches of one) and in a mix (four workers, batches of eight, all queued
+    at once, mixed with requests on the registered vertices)."""
+    import paper_2403_10647_gb300 as pg
+    reqs = _requests(32, len(pool), seed=91)
+    upd = [(_deformed(pool[m], k % 3) if k % 3 else None) for k, (m, _, _) in enumerate(reqs)]
+
+    def serve(srv, serial):
+        ids = [srv.register(s.verts, s.tris, s.lam) for s in pool]
+        out, tks = [], []
+        for (m, s, sd), u in zip(reqs, upd):
+            tk = srv.submit(ids[m], s, sd, verts=u)
+            if serial:
+                r = srv.wait(tk, timeout=120)
+                out.append((host(r.cells), host(r.refs), r.info))
+                r.release()
+            else:
+                tks.append(tk)
+        for tk in tks:
+            r = srv.wait(tk, timeout=120)
+            out.append((host(r.cells), host(r.refs), r.info))
+            r.release()
+        return out, srv.stats()
+
+    a_srv = pg.Server(0, nworkers=1, max_batch=1)
+    try:
+        alone, _ = serve(a_srv, True)
+    finally:
+        a_srv.close()
+    m_srv = pg.Server(0, nworkers=4, max_batch=8)
+    try:
+        mixed, st = serve(m_srv, False)
+    finally:
+        m_srv.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    for k, ((ca, ra, ia), (cb, rb, ib)) in enumerate(zip(alone, mixed)):
+        assert ia == ib, k
+        assert np.array_equal(ca, cb) and np.array_equal(ra, rb), f"request {k} differs in the mix"
+    # and both equal the oracle on a sample
+    for k in (0, 1, 2, 5):
+        m, s, sd = reqs[k]
+        sc = pool[m]
+        o = _update_oracle(sc, sc.verts if upd[k] is None else upd[k], s, sd)
+        assert np.array_equal(alone[k][0], o.G) and np.array_equal(alone[k][1], o.refs), k
+
+
+def test_bad_vertex_updates(ctx, pool):
+    """A non-finite update fails its request alone (GRID_EINVAL); a wrong
+    vertex count is refused by the binding before the C call."""
+    import paper_2403_10647_gb300 as pg
+    from paper_2403_10647_gb300 import _lib
+    sc = pool[0]
+    srv = pg.Server(0, nworkers=1, max_batch=4)
+    try:
+        mid = srv.register(sc.verts, sc.tris, sc.lam)
+        bad = _deformed(sc, 1)
+        bad[int(sc.tris[7, 1]), 2] = np.inf
+        t_bad = srv.submit(mid, 0.0, 0, verts=bad)
+        t_ok = srv.submit(mid, 0.0, 0, verts=_deformed(sc, 2))
+        with pytest.raises(pg.GridError) as e:
+            srv.wait(t_bad, timeout=120)
+        assert e.value.code == _lib.GRID_EINVAL
+        assert srv.release(t_bad) == 0
+        r = srv.wait(t_ok, timeout=120)
+        assert_same_as_oracle(r, _update_oracle(sc, _deformed(sc, 2), 0.0, 0), "good update after a bad one")
+        r.release()
+        with pytest.raises(ValueError):
+            srv.submit(mid, 0.0, 0, verts=_deformed(sc, 1)[:-1])
+        assert srv.stats()["reserved_bytes"] == 0
+    finally:
+        srv.close()
