@@ -40,7 +40,9 @@ SymbolAddrs g_addrs[kMaxDevices];
 std::mutex g_addrs_mutex;
 
 // Device addresses of the scratch arrays on the current device, looked up
-// once per device (the host-side names are not device addresses).
+// once per device (the host-side names are not device addresses) and kept
+// for the life of the process: a cudaDeviceReset in between would leave them
+// stale, which the header documents as a limit of this entry point.
 int scratch_addresses(int dev, SymbolAddrs *out)
 {
     if (dev < 0 || dev >= kMaxDevices) return GRID_EINVAL;

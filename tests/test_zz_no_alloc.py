@@ -4,13 +4,17 @@ manager, loops where an allocation would synchronise the device, paths that
 must not run out of memory once initialised).
 
 It is checked through the C ABI against grid_extract_ranges (the entry point
-that allocates its scratch from a context), bit for bit, on two calls in a
-row that reuse its fixed scratch array.  This file sorts last so that a run
+that allocates its scratch from a context) and against the CPU oracle's
+ranges, bit for bit, on two calls in a row that reuse its fixed scratch
+array; a rejected call (a key outside the grid) must not spoil the next one,
+which shares the same error word.  This file sorts last so that a run
 stopping at the first failure has already run every other test."""
 import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -45,8 +49,29 @@ def test_noalloc_matches_allocating_entry_point_twice(ctx):
         rc, got = _noalloc(lib, C, ncells)
         assert rc == _lib.GRID_OK, lib.grid_strerror(rc)
         want = ctx.extract_ranges(C, ncells)
-        assert torch.equal(got, want), f"case {seed}: ranges differ"
+        assert torch.equal(got, want), f"case {seed}: ranges differ from grid_extract_ranges"
+        assert np.array_equal(got.cpu().numpy(), oracle.ranges(C.cpu().numpy(), ncells)), \
+            f"case {seed}: ranges differ from the oracle"
         assert int(got[-1]) == count and int(got[0]) == 0
+
+
+def test_noalloc_error_does_not_leak_into_the_next_call(ctx):
+    """A key equal to ncells is rejected (GRID_EINVAL); the error word it set
+    is shared by every call, so the valid call right after must still return
+    GRID_OK with the right ranges."""
+    from paper_2403_10647_gb300 import _lib
+    lib = _lib.load()
+    ncells = 50_000
+    keys = _sorted_keys(3, 200_000, ncells, False)
+    bad = keys.copy()
+    bad[-1] = ncells
+    rc, _ = _noalloc(lib, torch.from_numpy(bad).cuda(), ncells)
+    assert rc == _lib.GRID_EINVAL, lib.grid_strerror(rc)
+    C = torch.from_numpy(keys).cuda()
+    rc, got = _noalloc(lib, C, ncells)
+    assert rc == _lib.GRID_OK, lib.grid_strerror(rc)
+    assert torch.equal(got, ctx.extract_ranges(C, ncells))
+    assert np.array_equal(got.cpu().numpy(), oracle.ranges(keys, ncells))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(ctx):
