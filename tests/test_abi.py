@@ -109,7 +109,7 @@ def test_null_arguments_rejected(lib):
 def test_null_arguments_rejected_serving(lib):
     tk = ctypes.c_uint64()
     assert lib.grid_serve_create(0, None, None) == _lib.GRID_EINVAL
-    assert lib.grid_serve_submit(None, 0, 0.0, 0, ctypes.byref(tk)) == _lib.GRID_EINVAL
+    assert lib.grid_serve_submit(None, 0, None, 0.0, 0, ctypes.byref(tk)) == _lib.GRID_EINVAL
     assert lib.grid_serve_poll(None, 1, None, None, None) == _lib.GRID_EINVAL
     assert lib.grid_serve_wait(None, 1, 0, None, None, None) == _lib.GRID_EINVAL
     assert lib.grid_serve_release(None, 1) == _lib.GRID_EINVAL
