@@ -114,7 +114,17 @@ typedef struct {
                              give the same grid.  0: 256 threads x 12 pairs (the default; fastest
                              on large, dense scenes), 1: 384 threads x 8 pairs (more warps per tile;
                              faster on sparse and small scenes).  grid_ctx_autotune picks one */
-    int32_t reserved[4];
+    int32_t local_bits;   /* how builds finish RadixSort and the range steps.  The hybrid: radix
+                             passes over the high key bits only, then one counting sort per bucket
+                             of 2^L consecutive cells in shared memory, which also writes the
+                             bucket's cell ranges.  The chain: radix passes over every key bit,
+                             then range extraction (the paper's).  0 (default): the hybrid at up to
+                             6 pairs per cell, with L chosen per build from the key width and the
+                             pairs per cell, the chain otherwise.  -2: the hybrid always, L chosen
+                             per build.  1..11: the hybrid always with that L (fewer radix passes,
+                             larger buckets).  -1: the chain always.  Every setting gives the same
+                             grid */
+    int32_t reserved[3];
 } grid_opts;
 
 /* ---- context -------------------------------------------------------------- */
@@ -137,8 +147,9 @@ const char *grid_version(void);
  * inputs read once, outputs written once).  Launches are counted always. */
 typedef struct {
     char name[32];        /* kernel family: bounds, count_scan, tile_search, emit, upsweep_gen,
-                             downsweep_gen, upsweep, downsweep, extract_split, extract, localize,
-                             make_pairs_per_object, cull_emit */
+                             downsweep_gen, upsweep, downsweep, downsweep_first, extract_split,
+                             extract, bucket_split, local_sort, localize, make_pairs_per_object,
+                             cull_emit */
     int64_t launches;
     double total_ms;      /* sum of event-timed durations (0 when profiling is off) */
     double bytes;         /* sum of algorithmic bytes */
@@ -149,16 +160,28 @@ typedef struct {
  * later builds.  First every radix digit width (8, 9, 10, 11 bits) x pair
  * generation (GRID_PAIRS_FUSED, GRID_PAIRS_EMIT) with the context's block
  * shape, then the other block shape (grid_opts.tile_shape) with the best of
- * those.  Each candidate is timed with CUDA events on the context's stream:
- * the median of `reps` builds after one warm-up (reps <= 0 means 3).  Every
- * candidate gives the same grid, so tuning changes speed only.  *chosen
- * (may be NULL) gets the kept radix_bits, pair_gen and tile_shape; times
- * (may be NULL, 9 entries) the median ms of each candidate: radix 8..11 x
- * (FUSED, EMIT), then the other shape.  The culling setting is left as it
- * is.  Errors as grid_build; on error the context keeps its previous
- * setting. */
+ * those, then the other end of the sort (grid_opts.local_bits: radix passes
+ * over every key bit and range extraction if the context's setting picks
+ * the hybrid for this mesh, the hybrid otherwise: local_bits -1 or -2).  Each
+ * candidate is timed with CUDA events on the context's stream: the median of
+ * `reps` builds after one warm-up (reps <= 0 means 3).  Every candidate gives
+ * the same grid, so tuning changes speed only.  *chosen (may be NULL) gets
+ * the kept radix_bits, pair_gen, tile_shape and local_bits; times (may be
+ * NULL, 10 entries) the median ms of each candidate: radix 8..11 x (FUSED,
+ * EMIT), then the other shape, then the other sort end.  The culling setting
+ * is left as it is.  Errors as grid_build; on error the context keeps its
+ * previous setting. */
 int grid_ctx_autotune(grid_ctx *ctx, const float *verts, int64_t nverts, const int32_t *tris, int64_t n,
                       float lambda, int32_t reps, grid_opts *chosen, double *times);
+
+/* How the context's builds would finish RadixSort for `count` pairs over
+ * `ncells` cells with key_bits-bit keys (grid_opts.local_bits): *local_bits
+ * gets L (the cell bits each per-bucket counting sort covers; -1 when every
+ * key bit goes through radix passes, the paper's chain with range
+ * extraction) and *passes the number of radix passes over the key bits
+ * above L (may be NULL).  Host only. */
+int grid_ctx_sort_plan(grid_ctx *ctx, int32_t key_bits, int64_t count, int64_t ncells, int32_t *local_bits,
+                       int32_t *passes);
 
 /* Turns event timing on (1) or off (0) and clears the statistics. */
 int grid_ctx_profile(grid_ctx *ctx, int enable);
@@ -220,6 +243,17 @@ typedef struct {
  * (bounds, pair count) and at the end. */
 int grid_build_batched(grid_ctx *ctx, const grid_mesh *meshes, int32_t nmeshes, grid_buf *out_cells,
                        grid_buf *out_refs, grid_info *infos, int64_t *cells_offsets, int64_t *refs_offsets);
+
+/* The autotuner for batches (the many-mesh builds of grid_build_batched):
+ * times the batch `meshes` built as one with every radix digit width (8..11
+ * bits), then the other block shape with the best width, then the other end
+ * of the sort (as grid_ctx_autotune), and keeps the fastest for the
+ * context's later builds.  Timing, reps, chosen and errors as
+ * grid_ctx_autotune (pair_gen is reported as GRID_PAIRS_FUSED: batched
+ * builds always generate the pairs in the first radix pass); times (may be
+ * NULL, 6 entries): radix 8..11, the other shape, the other sort end. */
+int grid_ctx_autotune_batched(grid_ctx *ctx, const grid_mesh *meshes, int32_t nmeshes, int32_t reps,
+                              grid_opts *chosen, double *times);
 
 /* ---- the steps one by one (device pointers, caller-allocated outputs) ----- */
 

@@ -124,7 +124,13 @@ class Context:
     TILE_SHAPE = {"256x12": 0, "384x8": 1}
 
     def __init__(self, device: int = 0, radix_bits: int = 0, pair_gen: str = "fused", cull: bool = False,
-                 tile_shape: str = "256x12"):
+                 tile_shape: str = "256x12", local_bits: int = 0):
+        """local_bits: how builds finish the sort and the range steps (see
+        grid_opts.local_bits): 0 (default) = the hybrid (radix passes over the
+        high key bits, then a per-bucket counting sort that also writes the
+        cell ranges) at up to 6 pairs per cell, else radix passes over every
+        key bit and range extraction; -2 = the hybrid always; 1..11 = the
+        hybrid with that many cell bits per bucket; -1 = never."""
         import torch
         self._torch = torch
         self.device = torch.device("cuda", device)
@@ -134,6 +140,7 @@ class Context:
         opts.pair_gen = self.PAIR_GEN[pair_gen]
         opts.cull = 1 if cull else 0
         opts.tile_shape = self.TILE_SHAPE[tile_shape]
+        opts.local_bits = int(local_bits)
         h = ctypes.c_void_p()
         check(self._lib.grid_ctx_create(int(device), ctypes.byref(opts), ctypes.byref(h)), "grid_ctx_create")
         self._h = h
@@ -172,15 +179,17 @@ class Context:
     def autotune(self, verts, tris, lam: float, reps: int = 3) -> dict:
         """Times every radix width (8..11) x pair generation (fused, emit) on
         this mesh, then the other radix-kernel block shape with the best of
-        them, and keeps the fastest for later builds (same grid either way).
-        Returns {"radix_bits", "pair_gen", "tile_shape",
-        "times_ms": {(bits, mode): ms, "other_shape": ms}}."""
+        them, then the other end of the sort (per-bucket counting sort or all
+        radix passes), and keeps the fastest for later builds (same grid
+        either way).  Returns {"radix_bits", "pair_gen", "tile_shape",
+        "local_bits", "times_ms": {(bits, mode): ms, "other_shape": ms,
+        "other_sort_end": ms}}."""
         torch = self._torch
         v = self._dev(verts, torch.float32, 3)
         t = self._dev(tris, torch.int32, 3)
         self._bind_stream()
         chosen = GridOpts()
-        times = (ctypes.c_double * 9)()
+        times = (ctypes.c_double * 10)()
         check(self._lib.grid_ctx_autotune(self._h, v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], float(lam),
                                           int(reps), ctypes.byref(chosen), times), "grid_ctx_autotune")
         names = {v: k for k, v in self.PAIR_GEN.items()}
@@ -191,9 +200,52 @@ class Context:
                 tt[(rb, mode)] = float(times[k])
                 k += 1
         tt["other_shape"] = float(times[8])
+        tt["other_sort_end"] = float(times[9])
         shapes = {v: k for k, v in self.TILE_SHAPE.items()}
         return {"radix_bits": int(chosen.radix_bits), "pair_gen": names[int(chosen.pair_gen)],
-                "tile_shape": shapes[int(chosen.tile_shape)], "times_ms": tt}
+                "tile_shape": shapes[int(chosen.tile_shape)], "local_bits": int(chosen.local_bits),
+                "times_ms": tt}
+
+    def _mesh_array(self, meshes):
+        torch = self._torch
+        keep = []
+        arr = (_lib.GridMesh * len(meshes))()
+        for m, (verts, tris, lam) in enumerate(meshes):
+            v = self._dev(verts, torch.float32, 3)
+            t = self._dev(tris, torch.int32, 3)
+            keep += [v, t]
+            arr[m].verts, arr[m].nverts = v.data_ptr(), v.shape[0]
+            arr[m].tris, arr[m].n, arr[m].lam = t.data_ptr(), t.shape[0], float(lam)
+        return arr, keep
+
+    def autotune_batched(self, meshes, reps: int = 3) -> dict:
+        """Times the batch `meshes` ((verts, tris, lam) each) built as one with
+        every radix width (8..11), then the other block shape, then the other
+        end of the sort, and keeps the fastest for later builds.  Returns
+        {"radix_bits", "tile_shape", "local_bits", "times_ms": {bits: ms,
+        "other_shape": ms, "other_sort_end": ms}}."""
+        arr, keep = self._mesh_array(meshes)
+        self._bind_stream()
+        chosen = GridOpts()
+        times = (ctypes.c_double * 6)()
+        check(self._lib.grid_ctx_autotune_batched(self._h, arr, len(meshes), int(reps), ctypes.byref(chosen), times),
+              "grid_ctx_autotune_batched")
+        del keep
+        tt = {rb: float(times[rb - 8]) for rb in range(8, 12)}
+        tt["other_shape"] = float(times[4])
+        tt["other_sort_end"] = float(times[5])
+        shapes = {v: k for k, v in self.TILE_SHAPE.items()}
+        return {"radix_bits": int(chosen.radix_bits), "tile_shape": shapes[int(chosen.tile_shape)],
+                "local_bits": int(chosen.local_bits), "times_ms": tt}
+
+    def sort_plan(self, key_bits: int, count: int, ncells: int) -> tuple:
+        """(local bits L, radix passes) this context's builds use for
+        `count` pairs over `ncells` cells with key_bits-bit keys; L = -1
+        when every key bit goes through radix passes."""
+        lb, p = ctypes.c_int32(), ctypes.c_int32()
+        check(self._lib.grid_ctx_sort_plan(self._h, int(key_bits), int(count), int(ncells), ctypes.byref(lb),
+                                           ctypes.byref(p)), "grid_ctx_sort_plan")
+        return int(lb.value), int(p.value)
 
     def profile(self, enable: bool = True) -> None:
         """Per-kernel CUDA-event timing on (clears the statistics)."""
@@ -201,9 +253,9 @@ class Context:
 
     def kernel_stats(self) -> dict:
         """{kernel family: {"launches", "ms", "bytes"}} since the last profile() call."""
-        arr = (_lib.GridKernelStat * 16)()
+        arr = (_lib.GridKernelStat * 32)()
         n = ctypes.c_int()
-        check(self._lib.grid_ctx_kernel_stats(self._h, arr, 16, ctypes.byref(n)), "grid_ctx_kernel_stats")
+        check(self._lib.grid_ctx_kernel_stats(self._h, arr, 32, ctypes.byref(n)), "grid_ctx_kernel_stats")
         return {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].total_ms),
                                        "bytes": float(arr[i].bytes)} for i in range(n.value)}
 
@@ -229,15 +281,7 @@ class Context:
         Returns a sequence with one Grid per mesh whose cells / refs are views
         into two library buffers (bit-identical to building each mesh
         alone); a mesh's views are made when it is first accessed."""
-        torch = self._torch
-        keep = []
-        arr = (_lib.GridMesh * len(meshes))()
-        for m, (verts, tris, lam) in enumerate(meshes):
-            v = self._dev(verts, torch.float32, 3)
-            t = self._dev(tris, torch.int32, 3)
-            keep += [v, t]
-            arr[m].verts, arr[m].nverts = v.data_ptr(), v.shape[0]
-            arr[m].tris, arr[m].n, arr[m].lam = t.data_ptr(), t.shape[0], float(lam)
+        arr, keep = self._mesh_array(meshes)
         nm = len(meshes)
         infos = (GridInfo * nm)()
         coff = (ctypes.c_int64 * nm)()

@@ -57,7 +57,7 @@ class GridKernelStat(ctypes.Structure):
 
 class GridOpts(ctypes.Structure):
     _fields_ = [("radix_bits", c_int32), ("pair_gen", c_int32), ("cull", c_int32), ("tile_shape", c_int32),
-                ("reserved", c_int32 * 4)]
+                ("local_bits", c_int32), ("reserved", c_int32 * 3)]
 
 
 class GridServeOpts(ctypes.Structure):
@@ -83,8 +83,11 @@ SIGNATURES = {
     "grid_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "grid_version": (ctypes.c_char_p, []),
     "grid_ctx_profile": (c_int32, [c_void_p, ctypes.c_int]),
+    "grid_ctx_sort_plan": (c_int32, [c_void_p, c_int32, c_int64, c_int64, P(c_int32), P(c_int32)]),
     "grid_ctx_autotune": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_float, c_int32, P(GridOpts),
                                     P(ctypes.c_double)]),
+    "grid_ctx_autotune_batched": (c_int32, [c_void_p, P(GridMesh), c_int32, c_int32, P(GridOpts),
+                                            P(ctypes.c_double)]),
     "grid_ctx_kernel_stats": (c_int32, [c_void_p, c_void_p, ctypes.c_int, P(ctypes.c_int)]),
     "grid_build": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_float, P(GridBuf), P(GridBuf),
                              P(GridInfo)]),

@@ -15,6 +15,9 @@ constexpr unsigned ERR_OVERFLOW = 4u;   // a prefix sum passed INT32_MAX
 constexpr unsigned ERR_TIMEOUT = 8u;    // a bounded look-back wait gave up
 constexpr unsigned ERR_RANGE = 16u;     // a key outside [0, ncells) or out of order reached range
                                         // extraction, or a sort scatter fell outside the output
+constexpr unsigned ERR_LOCAL_FALLBACK = 32u;   // not an error: a group of buckets too large for the
+                                               // per-bucket counting sort; the host places the build
+                                               // by radix passes over every key bit instead
 
 // Spin limit of every look-back wait (each iteration sleeps ~0.1-1 us).
 constexpr unsigned SPIN_LIMIT = 1u << 20;
@@ -29,7 +32,8 @@ struct Ctl {
     unsigned err;               // ERR_* bits
     unsigned spare;             // unused (keeps the layout)
     unsigned long long nrefs;   // NO, written by the last count/scan tile
-    unsigned tickets[8];        // tile tickets: [0] count/scan, [7] culling emit
+    unsigned tickets[8];        // tile tickets: [0] count/scan, [7] culling emit; [2] counts the
+                                // hybrid placement's bucket groups
     unsigned long long nkept;   // pairs the culling emit kept, written by its last tile
     unsigned pad[4];
 };

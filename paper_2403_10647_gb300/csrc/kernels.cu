@@ -1075,7 +1075,13 @@ __device__ __forceinline__ bool mbar_wait_phase0(unsigned long long *bar)
     return false;
 }
 
-template <int BLOCK, int ITEMS, int RBITS, int IN>
+// STABLE: rank equal digits in element order (every pass of a plain LSD
+// sort).  Otherwise equal digits of one warp may be ranked in any order: the
+// first pass of the hybrid placement, whose only job is to order the pairs by
+// its digit (the later passes need that order, not the order inside a
+// digit, and the per-bucket counting sort puts each cell's objects in
+// ascending order at the end).
+template <int BLOCK, int ITEMS, int RBITS, int IN, bool STABLE>
 __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_kernel(DownArgs a, unsigned gtiles)
 {
     constexpr int W = BLOCK / 32;
@@ -1151,7 +1157,8 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_ker
             keys[i] = e < cnt ? __ldcs(a.keys_in + j0 + e) : 0u;
         }
     }
-    for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
+    if (STABLE)
+        for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
     __syncthreads();
 
     // warp-level multisplit, stable in element order (items in order,
@@ -1163,8 +1170,36 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_ker
     // shared-memory round trips overlap; the reservations are issued in
     // item order, which keeps the ranks stable.
     unsigned ranks[ITEMS / 2];   // 16-bit ranks, two per register
+    if (!STABLE) {
+        // runs of equal digits in consecutive lanes (pairs of one object often
+        // share the high digits): the run's first lane reserves the run's
+        // slots with one shared atomic and the others count from it
+        const unsigned lemask = ltmask | bit;
 #pragma unroll
-    for (int ib = 0; ib < ITEMS; ib += BATCH) {
+        for (int i = 0; i < ITEMS; ++i) {
+            const unsigned e = w * 32 * ITEMS + i * 32 + lane;
+            const bool ok = e < cnt;
+            const unsigned d = ok ? (keys[i] >> sh) & mk : 0xFFFFFFFFu;   // the tail forms a run of its own
+            const unsigned dprev = __shfl_up_sync(0xffffffffu, d, 1);
+            const bool head = lane == 0 || d != dprev;
+            const unsigned hm = __ballot_sync(0xffffffffu, head);
+            const unsigned start = 31u - __clz(hm & lemask);
+            const unsigned above = hm & ~lemask;
+            const unsigned end = above ? (unsigned)__ffs(above) - 1u : 32u;
+            unsigned old = 0u;
+            if (head && ok) {
+                const unsigned hs = (d & 1u) * 16u;
+                old = (atomicAdd(&s_wh32[(w * R + d) >> 1], (end - start) << hs) >> hs) & 0xFFFFu;
+            }
+            const unsigned r = __shfl_sync(0xffffffffu, old, start) + (lane - start);
+            if (i % 2 == 0)
+                ranks[i / 2] = r;
+            else
+                ranks[i / 2] |= r << 16;
+        }
+    }
+#pragma unroll
+    for (int ib = 0; ib < (STABLE ? ITEMS : 0); ib += BATCH) {
         unsigned d[BATCH], peers[BATCH], old[BATCH];
         bool ok[BATCH];
 #pragma unroll
@@ -1388,6 +1423,253 @@ __global__ void __launch_bounds__(BLOCK) extract_kernel(ExtractArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// a8 (low digits) + a9 per bucket: counting sort by cell, cell ranges
+// ---------------------------------------------------------------------------
+//
+// The radix passes have ordered the pairs by key >> lbits, so each bucket of
+// 2^lbits consecutive cells is one contiguous run of pairs.  Consecutive
+// buckets are grouped (a group closes where the running pair count crosses
+// a multiple of group_pairs, or at 2^LOCAL_LMAX cells), and one block per
+// group counts the group's pairs per cell with shared-memory atomics (the
+// value an atomic returns is the pair's slot inside its cell), scans the
+// counts into the cells' offsets (G of the group's cells, less the group's
+// first pair), and puts every pair at its cell's offset plus its slot.  The
+// slots of a cell come out in no fixed order; the pairs of one cell belong to
+// distinct objects, and the stable sort of object-order pairs leaves them in
+// ascending object order, so each cell's run is put in ascending order
+// afterwards.  The result is the stable sort's, bit for bit.
+
+// Does bucket b open a group?  sp, sb, sn: starts of buckets b - 1, b and
+// b + 1.  A group closes where the running pair count crosses a multiple of
+// group_pairs, at every bmax-th bucket (2^LOCAL_LMAX cells at most), and
+// around every bucket of more than LOCAL_CAP - group_pairs pairs, which
+// forms a group of its own; so no group holds more than LOCAL_CAP pairs
+// unless one bucket alone does.
+__device__ __forceinline__ bool opens_group(unsigned b, unsigned sp, unsigned sb, unsigned sn,
+                                            unsigned group_pairs, unsigned bmax)
+{
+    const unsigned big = (unsigned)LOCAL_CAP - group_pairs;
+    return b == 0u || b % bmax == 0u || sp / group_pairs != sb / group_pairs || sb - sp > big || sn - sb > big;
+}
+
+// First pair of bucket b (b <= nbuckets): the number of keys whose bucket is
+// below b.
+__device__ __forceinline__ unsigned bucket_start(const LocalArgs &a, unsigned b)
+{
+    if (b >= a.nbuckets) return a.count;
+    unsigned lo = 0, hi = a.count;
+    while (lo < hi) {
+        const unsigned mid = lo + ((hi - lo) >> 1);
+        if ((__ldg(a.keys + mid) >> a.lbits) < b)
+            lo = mid + 1u;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) bucket_split_kernel(LocalArgs a)
+{
+    const unsigned b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > a.nbuckets) return;
+    const unsigned sb = bucket_start(a, b);
+    a.starts[b] = sb;
+    if (b == a.nbuckets) {
+        a.G[a.ncells] = a.count;
+        return;
+    }
+    const unsigned bmax = (1u << LOCAL_LMAX) >> a.lbits;
+    const unsigned sp = b ? bucket_start(a, b - 1u) : 0u, sn = bucket_start(a, b + 1u);
+    if (opens_group(b, sp, sb, sn, a.group_pairs, bmax)) {
+        const unsigned g = atomicAdd(&a.ctl->tickets[2], 1u);
+        if (g < a.max_groups)
+            a.groups[g] = b;
+        else
+            atomicOr(&a.ctl->err, ERR_RANGE);   // never: max_groups bounds the groups
+    }
+}
+
+// In place: h[0 .. n) becomes its exclusive prefix sums and h[n] their total.
+// Ends with a barrier.
+template <int BLOCK>
+__device__ __forceinline__ void scan_counts(unsigned *h, unsigned n, unsigned *s_tmp)
+{
+    const unsigned per = (n + BLOCK - 1) / BLOCK;
+    const unsigned c0 = min(threadIdx.x * per, n), c1 = min(c0 + per, n);
+    unsigned sum = 0;
+    for (unsigned c = c0; c < c1; ++c) sum += h[c];
+    unsigned tot;
+    unsigned ex = block_excl_sum<BLOCK>(sum, s_tmp, &tot);
+    for (unsigned c = c0; c < c1; ++c) {
+        const unsigned v = h[c];
+        h[c] = ex;
+        ex += v;
+    }
+    if (threadIdx.x == 0) h[n] = tot;
+    __syncthreads();
+}
+
+// Position of the set bit of `bits` (one bit per position) at or before j,
+// and of the first one after j (n if none before n): the run of the cell
+// whose bit marks its start.
+__device__ __forceinline__ unsigned run_start(const unsigned *bits, unsigned j)
+{
+    unsigned w = j >> 5;
+    unsigned x = bits[w] & (0xFFFFFFFFu >> (31u - (j & 31u)));   // bits <= j
+    while (x == 0u) x = bits[--w];   // position 0 always opens a run
+    return (w << 5) + 31u - __clz(x);
+}
+
+__device__ __forceinline__ unsigned run_end(const unsigned *bits, unsigned j, unsigned n)
+{
+    unsigned w = j >> 5;
+    unsigned x = (j & 31u) == 31u ? 0u : bits[w] & (0xFFFFFFFEu << (j & 31u));   // bits > j
+    const unsigned last = (n - 1u) >> 5;
+    while (x == 0u && w < last) x = bits[++w];
+    return x ? min((w << 5) + (unsigned)__ffs(x) - 1u, n) : n;
+}
+
+// One block per group of buckets, in passes over the group's pairs: count
+// them per cell (shared atomics), scan the counts into the cells' offsets
+// (written out as G), then place the pairs cell by cell in shared memory
+// (atomics on per-cell cursors hand out slots inside a cell in no fixed
+// order) and write each pair to its cell's offset plus its rank among the
+// cell's pairs by object id: the order a stable sort of object-order pairs
+// leaves them in.  A group of more than LOCAL_CAP pairs is placed in chunks
+// of whole cells (each chunk gathers its pairs in one more pass over the
+// group).  A group with a cell of more than LOCAL_RUN_MAX pairs is left
+// alone and flagged ERR_LOCAL_FALLBACK: the host then places the whole build
+// by radix passes over every key bit and range extraction instead.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, LOCAL_MIN_BLOCKS) local_sort_kernel(LocalArgs a)
+{
+    constexpr int HN = 1 << LOCAL_LMAX;
+    constexpr unsigned Q = (unsigned)LOCAL_CAP - LOCAL_RUN_MAX;   // chunk k: cells with offsets in [k Q, (k + 1) Q)
+    extern __shared__ __align__(16) unsigned smem[];
+    unsigned *h = smem;                 // [HN + 1] per-cell counts, then offsets
+    unsigned *hc = h + HN + 1;          // [HN] per-cell cursors of the current chunk
+    unsigned *s_o = hc + HN;            // [LOCAL_CAP] the chunk's values, by cell
+    __shared__ unsigned s_bits[LOCAL_CAP / 32];   // one bit per position of s_o: a cell's run starts
+    __shared__ unsigned s_tmp[BLOCK / 32];
+    __shared__ unsigned s_end, s_flag, s_clo, s_chi;
+    const int tid = threadIdx.x;
+    const unsigned ngroups = min(ld_relaxed_u32(&a.ctl->tickets[2]), a.max_groups);
+    const unsigned bmax = (1u << LOCAL_LMAX) >> a.lbits;
+    // blocks take groups in turn: a fixed grid, no block without a group
+    for (unsigned g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    __syncthreads();   // the previous group's last reads of shared memory are done
+    const unsigned b0 = a.groups[g];
+    // the group's end: the next bucket that opens a group, at most bmax on
+    if (tid == 0) {
+        s_end = min(b0 + bmax, a.nbuckets);
+        s_flag = 0u;
+    }
+    __syncthreads();
+    for (unsigned b = b0 + 1u + tid; b < min(b0 + bmax, a.nbuckets); b += BLOCK) {
+        const unsigned sn = b + 1u < a.nbuckets ? a.starts[b + 1u] : a.count;
+        if (opens_group(b, a.starts[b - 1u], a.starts[b], sn, a.group_pairs, bmax)) atomicMin(&s_end, b);
+    }
+    __syncthreads();
+    const unsigned b1 = s_end;
+    const unsigned long long cbase64 = (unsigned long long)b0 << a.lbits;
+    const unsigned cbase = (unsigned)cbase64;
+    const unsigned nh = (b1 - b0) << a.lbits;   // cells of the whole buckets, <= HN
+    const unsigned nc = (unsigned)min((unsigned long long)nh, a.ncells - cbase64);   // cells inside the grid
+    const unsigned s = a.starts[b0], m = a.starts[b1] - s;
+    if (a.starts[b1] < s || nh > (unsigned)HN) {   // starts of sorted keys never decrease
+        if (tid == 0) atomicOr(&a.ctl->err, ERR_RANGE);
+        continue;
+    }
+    const unsigned *keys = a.keys + s, *vals = a.vals + s;
+    unsigned *refs = a.refs + s;
+    bool bad = false;
+    // count the pairs per cell.  The loops over the group's pairs take U
+    // pairs per thread at a time, every load issued before any is used.
+    constexpr int U = 8;
+    for (unsigned c = tid; c < nh; c += BLOCK) h[c] = 0u;
+    __syncthreads();
+    for (unsigned j0 = tid; j0 < m; j0 += U * BLOCK) {
+        unsigned kk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) kk[u] = j0 + u * BLOCK < m ? __ldg(keys + j0 + u * BLOCK) : cbase + nc;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned c = kk[u] - cbase;   // wraps below the group
+            if (c < nc)
+                atomicAdd(&h[c], 1u);
+            else
+                bad |= j0 + u * BLOCK < m;   // a key outside the group: the keys were not ordered by bucket
+        }
+    }
+    __syncthreads();
+    bool long_run = false;
+    for (unsigned c = tid; c < nc; c += BLOCK) long_run |= h[c] > LOCAL_RUN_MAX;
+    if (long_run) s_flag = 1u;
+    scan_counts<BLOCK>(h, nh, s_tmp);
+    if (s_flag) {
+        if (tid == 0) atomicOr(&a.ctl->err, ERR_LOCAL_FALLBACK);
+        continue;
+    }
+    for (unsigned c = tid; c < nc; c += BLOCK) a.G[cbase64 + c] = s + h[c];
+    const unsigned nchunks = m > (unsigned)LOCAL_CAP ? (m + Q - 1u) / Q : 1u;
+    for (unsigned k = 0; k < nchunks; ++k) {
+        unsigned clo = 0, chi = nc;
+        if (nchunks > 1u) {   // the chunk's cells: binary searches over the offsets
+            if (tid == 0) {
+                unsigned lo = 0, hi = nc;
+                while (lo < hi) {
+                    const unsigned mid = (lo + hi) >> 1;
+                    if (h[mid] < k * Q) lo = mid + 1u; else hi = mid;
+                }
+                s_clo = lo;
+                hi = nc;
+                while (lo < hi) {
+                    const unsigned mid = (lo + hi) >> 1;
+                    if (h[mid] < (k + 1u) * Q) lo = mid + 1u; else hi = mid;
+                }
+                s_chi = lo;
+            }
+            __syncthreads();
+            clo = s_clo;
+            chi = s_chi;
+        }
+        const unsigned base = h[clo], cm = h[chi] - base;   // the chunk's pairs: [base, base + cm)
+        for (unsigned w = tid; w < (cm + 31u) / 32u; w += BLOCK) s_bits[w] = 0u;
+        for (unsigned c = clo + tid; c < chi; c += BLOCK) hc[c] = h[c] - base;
+        __syncthreads();
+        for (unsigned c = clo + tid; c < chi; c += BLOCK) {
+            const unsigned p = h[c] - base;   // not hc[c]: placement below moves the cursors
+            if (h[c + 1] > h[c]) atomicOr(&s_bits[p >> 5], 1u << (p & 31u));
+        }
+        // place the chunk's pairs by cell (slots inside a cell in no fixed order)
+        for (unsigned j0 = tid; j0 < m; j0 += U * BLOCK) {
+            unsigned kk[U], vv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) kk[u] = j0 + u * BLOCK < m ? __ldg(keys + j0 + u * BLOCK) : cbase + nc;
+#pragma unroll
+            for (int u = 0; u < U; ++u) vv[u] = j0 + u * BLOCK < m ? __ldg(vals + j0 + u * BLOCK) : 0u;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const unsigned c = kk[u] - cbase;
+                if (c >= clo && c < chi) s_o[atomicAdd(&hc[c], 1u)] = vv[u];
+            }
+        }
+        __syncthreads();
+        // each pair to its cell's start plus its rank by object id inside the cell
+        for (unsigned j = tid; j < cm; j += BLOCK) {
+            const unsigned v = s_o[j];
+            const unsigned lo = run_start(s_bits, j), hi = run_end(s_bits, j, cm);
+            unsigned r = 0;
+            for (unsigned i = lo; i < hi; ++i) r += s_o[i] < v ? 1u : 0u;
+            __stcs(refs + base + lo + r, v);
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(&a.ctl->err, ERR_RANGE);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // batched builds: per-mesh bounds, per-mesh cell arrays
 // ---------------------------------------------------------------------------
 
@@ -1588,11 +1870,11 @@ static cudaError_t launch_up_t(const UpArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int RBITS, int IN, int BLOCK>
+template <int RBITS, int IN, int BLOCK, bool STABLE = true>
 static cudaError_t launch_down_t(const DownArgs &a, unsigned ntiles, unsigned gtiles, cudaStream_t s)
 {
     constexpr int ITEMS = PAIR_TILE / BLOCK;
-    auto k = downsweep_kernel<BLOCK, ITEMS, RBITS, IN>;
+    auto k = downsweep_kernel<BLOCK, ITEMS, RBITS, IN, STABLE>;
     constexpr size_t smem = down_smem_bytes<BLOCK, ITEMS, RBITS>();
     static std::atomic<unsigned long long> configured{0};
     if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
@@ -1628,10 +1910,11 @@ template <int BLOCK>
 static cudaError_t launch_down_b(const DownArgs &a, int rbits, int in, unsigned ntiles, unsigned gtiles,
                                  cudaStream_t s)
 {
-#define GG_DOWN(RB)                                                                  \
-    case RB:                                                                         \
-        return in == IN_GEN ? launch_down_t<RB, IN_GEN, BLOCK>(a, ntiles, gtiles, s)  \
-                            : launch_down_t<RB, IN_PAIR, BLOCK>(a, ntiles, gtiles, s);
+#define GG_DOWN(RB)                                                                                     \
+    case RB:                                                                                            \
+        return in == IN_GEN    ? launch_down_t<RB, IN_GEN, BLOCK>(a, ntiles, gtiles, s)                 \
+               : in == IN_PAIR ? launch_down_t<RB, IN_PAIR, BLOCK>(a, ntiles, gtiles, s)                \
+                               : launch_down_t<RB, IN_PAIR, BLOCK, false>(a, ntiles, gtiles, s);
     switch (rbits) {
         GG_DOWN(8)
         GG_DOWN(9)
@@ -1659,6 +1942,30 @@ cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntil
     if (shape == SHAPE_MAIN) return launch_down_b<PAIR_BLOCK>(a, rbits, in, ntiles, gtiles, s);
     if (shape == SHAPE_ALT) return launch_down_b<ALT_BLOCK>(a, rbits, in, ntiles, gtiles, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bucket_split(const LocalArgs &a, cudaStream_t s)
+{
+    bucket_split_kernel<<<(a.nbuckets + 1 + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local_sort(const LocalArgs &a, cudaStream_t s)
+{
+    if (a.nbuckets == 0) return cudaSuccess;
+    if (a.lbits < 0 || a.lbits > LOCAL_LMAX) return cudaErrorInvalidValue;
+    auto k = local_sort_kernel<LOCAL_BLOCK>;
+    const size_t smem = sizeof(unsigned) * (2 * (1 << LOCAL_LMAX) + 1 + LOCAL_CAP);
+    static std::atomic<unsigned long long> configured{0};
+    if (cudaError_t e = allow_dynamic_smem(k, smem, configured)) return e;
+    if (a.max_groups == 0) return cudaSuccess;
+    // a grid of a few rounds of resident blocks; each block loops over groups
+    int dev = 0, nsm = 0;
+    if (cudaError_t e = cudaGetDevice(&dev)) return e;
+    if (cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) return e;
+    const unsigned grid = min(a.max_groups, (unsigned)(nsm * LOCAL_MIN_BLOCKS * 4));
+    k<<<grid, LOCAL_BLOCK, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells)

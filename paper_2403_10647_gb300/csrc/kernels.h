@@ -137,8 +137,10 @@ struct UpArgs {
     unsigned gtiles;                // tiles per group, 1 .. GROUP_TILES (group_tiles)
 };
 
-// Downsweep of one pass: stable rank and scatter of each tile.
-enum { IN_GEN = 0, IN_PAIR = 1 };
+// Downsweep of one pass: rank and scatter of each tile.  IN_PAIR_ANY reads
+// stored pairs like IN_PAIR but may rank equal digits of a warp out of
+// element order (the hybrid placement's first pass; see downsweep_kernel).
+enum { IN_GEN = 0, IN_PAIR = 1, IN_PAIR_ANY = 2 };
 
 struct DownArgs {
     const unsigned *keys_in;        // IN_PAIR
@@ -211,6 +213,49 @@ cudaError_t launch_upsweep(const UpArgs &a, int rbits, int src, int shape, cudaS
 // gtiles: the tiles per group of the pass's upsweep
 cudaError_t launch_downsweep(const DownArgs &a, int rbits, int in, unsigned ntiles, unsigned gtiles, int shape,
                              cudaStream_t s);
+// Hybrid placement: once the radix passes have ordered the pairs by the high
+// key bits (key >> lbits), every bucket of 2^lbits consecutive cells is a
+// contiguous run of pairs.  One block per bucket sorts its run by cell with a
+// counting sort in shared memory (RadixSort's low digits) and writes the
+// bucket's cell ranges G (RunLengthEncode + NonEmptyCells + ExclusiveSum)
+// and its object ids in cell order.
+#ifndef GG_LOCAL_BLOCK
+#define GG_LOCAL_BLOCK 512
+#endif
+#ifndef GG_LOCAL_CAP
+#define GG_LOCAL_CAP 12288
+#endif
+#ifndef GG_LOCAL_MIN_BLOCKS
+#define GG_LOCAL_MIN_BLOCKS 3
+#endif
+constexpr int LOCAL_BLOCK = GG_LOCAL_BLOCK;
+constexpr int LOCAL_CAP = GG_LOCAL_CAP;                 // pairs a block places at once
+constexpr int LOCAL_MIN_BLOCKS = GG_LOCAL_MIN_BLOCKS;   // resident blocks per SM it is compiled for
+constexpr int LOCAL_LMAX = 11;                          // at most 2^11 cells per bucket
+constexpr unsigned LOCAL_RUN_MAX = 512;                // longest cell run a block sorts
+constexpr unsigned LOCAL_GROUP_PAIRS = LOCAL_CAP / 2;  // pairs at which a group of buckets closes
+
+struct LocalArgs {
+    const unsigned *keys;           // [count] sorted by key >> lbits
+    const unsigned *vals;           // [count]
+    unsigned count;
+    unsigned long long ncells;
+    int lbits;                      // a bucket covers 2^lbits cells
+    unsigned nbuckets;
+    unsigned *starts;               // [nbuckets + 1]: first pair of each bucket (bucket_split)
+    unsigned *groups;               // [max_groups]: first bucket of each group, in no order
+    unsigned group_pairs;           // LOCAL_GROUP_PAIRS
+    unsigned max_groups;            // bound on the groups: blocks of the local sort
+    unsigned *refs;                 // [count] out: object ids in cell order
+    unsigned *G;                    // [ncells + 1] out
+    Ctl *ctl;                       // tickets[2] counts the groups (zero on entry)
+};
+
+// starts[b] = number of keys whose key >> lbits is below b, b = 0 .. nbuckets;
+// G[ncells] = count; the first bucket of every group appended to groups.
+cudaError_t launch_bucket_split(const LocalArgs &a, cudaStream_t s);
+cudaError_t launch_local_sort(const LocalArgs &a, cudaStream_t s);
+
 unsigned long long extract_blocks(unsigned long long count, unsigned long long ncells);
 cudaError_t launch_extract_split(const ExtractArgs &a, cudaStream_t s);
 cudaError_t launch_extract(const ExtractArgs &a, cudaStream_t s);

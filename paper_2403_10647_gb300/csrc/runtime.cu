@@ -18,6 +18,21 @@
 using gg::Ctl;
 using gg::ObjRec;
 
+// The hybrid placement's first radix pass may rank equal digits out of order
+// (1) or keeps them in order (0, for comparison).
+#ifndef GG_FIRST_ANY
+#define GG_FIRST_ANY 1
+#endif
+// Bits the hybrid placement's first radix pass takes beyond an even split
+// (its ranking is the cheaper one).
+#ifndef GG_FIRST_EXTRA
+#define GG_FIRST_EXTRA 0
+#endif
+#ifndef GG_LOCAL_PAIRS_PER_CELL
+#define GG_LOCAL_PAIRS_PER_CELL 6.0
+#endif
+constexpr double LOCAL_PAIRS_PER_CELL = GG_LOCAL_PAIRS_PER_CELL;
+
 namespace {
 
 constexpr int64_t kInt32Max = 0x7FFFFFFFll;
@@ -45,12 +60,12 @@ struct Scratch {
 
 enum KernelId {
     K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_LOCALIZE,
-    K_PER_OBJECT, K_CULL, K_NUM
+    K_PER_OBJECT, K_CULL, K_BSPLIT, K_LOCAL, K_DOWN_ANY, K_NUM
 };
 const char *const kKernelNames[K_NUM] = {"bounds",  "count_scan",    "tile_search",   "emit",
                                          "upsweep_gen", "downsweep_gen", "upsweep", "downsweep",
                                          "extract_split", "extract",   "localize", "make_pairs_per_object",
-                                         "cull_emit"};
+                                         "cull_emit", "bucket_split", "local_sort", "downsweep_first"};
 
 struct PendingTiming {
     int kid;
@@ -72,12 +87,16 @@ struct grid_ctx {
     int shape = 0;               // block shape of the radix kernels (gg::SHAPE_*)
     int pair_gen = GRID_PAIRS_FUSED;
     bool cull = false;
+    int local_bits = 0;          // grid_opts.local_bits
+    int64_t fallbacks = 0;       // hybrid placements redone by radix passes over every key bit
 
     Ctl *d_ctl = nullptr;        // device control block
     Ctl *h_ctl = nullptr;        // pinned host mirror
     unsigned *d_dbase = nullptr; // [MAX_PASSES][MAX_RADIX]
 
     Scratch recs, k2status, tile_obj, keys_sorted, keys[1], vals[1], intra, gpref, gstatus, splits;
+    Scratch vals_sorted, bstarts, bgroups;   // hybrid placement: last radix pass's values, bucket
+                                             // starts, bucket groups
     Scratch in_verts, in_tris, out_cells, out_refs;  // host-buffer builds
     Scratch b_desc, b_base, b_state, b_pairbase, b_cellsoff, b_G;   // batched builds
     Scratch pairs_C, pairs_O;    // object-order pairs of the unfused pair_gen modes and of culling
@@ -239,6 +258,7 @@ void resolve_timings(grid_ctx *c)
 // Error bits raised by the kernels -> GRID_* code.
 int ctl_error(unsigned err)
 {
+    err &= ~gg::ERR_LOCAL_FALLBACK;   // a request to the host, handled where it can arise
     if (err & (gg::ERR_BADINDEX | gg::ERR_NONFINITE | gg::ERR_RANGE)) return GRID_EINVAL;
     if (err & gg::ERR_OVERFLOW) return GRID_EOVERFLOW;
     if (err & gg::ERR_TIMEOUT) return GRID_ETIMEOUT;
@@ -316,21 +336,34 @@ int plan(const float lo[3], const float hi[3], int64_t n, float lambda, grid_inf
 // ---- radix-sort pass layout --------------------------------------------------
 struct SortCfg {
     int passes = 0;
-    int rbits = 8;  // kernel instantiation: widest digit, at least 8
+    int rbits = 8;  // widest kernel instantiation (sizes the per-tile tables)
+    int rb[gg::MAX_PASSES] = {8, 8, 8, 8};   // each pass's kernels: its digit width, at least 8
     int shift[gg::MAX_PASSES] = {0, 0, 0, 0};
     int bits[gg::MAX_PASSES] = {0, 0, 0, 0};
 };
 
-SortCfg sort_cfg(int key_bits, int rbits_max)
+// Passes over the key bits [lo_bit, key_bits): as few as digits of at most
+// rbits_max bits allow, the bits split as evenly as possible; first_extra
+// moves that many bits from the last pass to the first (at most up to
+// rbits_max).
+SortCfg sort_cfg(int key_bits, int rbits_max, int lo_bit = 0, int first_extra = 0)
 {
     SortCfg s;
-    if (key_bits <= 0) return s;
-    s.passes = (key_bits + rbits_max - 1) / rbits_max;
-    int sh = 0, widest = 0;
+    const int nbits = key_bits - lo_bit;
+    if (nbits <= 0) return s;
+    s.passes = (nbits + rbits_max - 1) / rbits_max;
+    int sh = lo_bit, widest = 0;
     for (int p = 0; p < s.passes; ++p) {
-        const int b = key_bits / s.passes + (p < key_bits % s.passes ? 1 : 0);
+        int b = nbits / s.passes + (p < nbits % s.passes ? 1 : 0);
+        if (s.passes > 1) {
+            const int base0 = nbits / s.passes + (nbits % s.passes ? 1 : 0);
+            const int e = std::max(0, std::min(std::min(first_extra, rbits_max - base0), nbits / s.passes - 1));
+            if (p == 0) b += e;
+            if (p == s.passes - 1) b -= e;
+        }
         s.shift[p] = sh;
         s.bits[p] = b;
+        s.rb[p] = std::max(8, b);
         sh += b;
         widest = std::max(widest, b);
     }
@@ -344,10 +377,13 @@ unsigned pair_tiles(int64_t count) { return (unsigned)((count + gg::PAIR_TILE - 
 // first pass generates the object-order pairs from recs/tile_obj; otherwise
 // it reads keys_in/vals_in.  The last pass writes keys_last / vals_last;
 // pass outputs alternate between those and one scratch pair of arrays so
-// the last lands there.
+// the last lands there.  first_any: the first pass need not keep equal
+// digits in input order (the hybrid placement restores the order inside
+// each cell itself).
 int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const ObjRec *recs, int64_t nobj,
                const unsigned *tile_obj, unsigned res_x, unsigned res_y, const gg::MeshTab &mt,
-               const unsigned *keys_in, const unsigned *vals_in, unsigned *keys_last, unsigned *vals_last)
+               const unsigned *keys_in, const unsigned *vals_in, unsigned *keys_last, unsigned *vals_last,
+               bool first_any = false)
 {
     const unsigned ntiles = pair_tiles(count);
     const unsigned gtiles = gg::group_tiles(ntiles, c->nsm);
@@ -412,7 +448,7 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         {
             KernelScope ks(c, gen_up ? K_UP_GEN : K_UP,
                            gen_up ? 16.0 * nobj + (store ? 8.0 * count : 0.0) : 4.0 * count);
-            GG_CUDA(gg::launch_upsweep(u, sc.rbits, gen_up ? gg::SRC_GEN : gg::SRC_MEM, c->shape, c->stream));
+            GG_CUDA(gg::launch_upsweep(u, sc.rb[p], gen_up ? gg::SRC_GEN : gg::SRC_MEM, c->shape, c->stream));
         }
         gg::DownArgs a{};
         a.keys_in = kin;
@@ -431,8 +467,10 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         a.gpref = (const unsigned *)c->gpref.ptr;
         a.intra = (const unsigned short *)c->intra.ptr;
         a.ctl = c->d_ctl;
-        KernelScope ks(c, gen_down ? K_DOWN_GEN : K_DOWN, gen_down ? 16.0 * nobj + 8.0 * count : 16.0 * count);
-        GG_CUDA(gg::launch_downsweep(a, sc.rbits, gen_down ? gg::IN_GEN : gg::IN_PAIR, ntiles, gtiles, c->shape,
+        const int in = gen_down ? gg::IN_GEN : (first && first_any ? gg::IN_PAIR_ANY : gg::IN_PAIR);
+        KernelScope ks(c, gen_down ? K_DOWN_GEN : (in == gg::IN_PAIR_ANY ? K_DOWN_ANY : K_DOWN),
+                       gen_down ? 16.0 * nobj + 8.0 * count : 16.0 * count);
+        GG_CUDA(gg::launch_downsweep(a, sc.rb[p], in, ntiles, gtiles, c->shape,
                                      c->stream));
     }
     return GRID_OK;
@@ -460,6 +498,163 @@ int extract_ranges(grid_ctx *c, const unsigned *keys, int64_t count, int64_t nce
     KernelScope ks(c, K_EXTRACT, 4.0 * count + 4.0 * (ncells + 1));
     GG_CUDA(gg::launch_extract(xa, c->stream));
     return GRID_OK;
+}
+
+// Does a build of `count` pairs over `ncells` cells use the hybrid placement
+// (radix passes over the high key bits, then the per-bucket counting sort)?
+// A context's local_bits decides (-1: never; -2 or 1..11: always); by
+// default (0) it is used at up to LOCAL_PAIRS_PER_CELL pairs per cell: with
+// more, the cells' runs are long and ordering them inside a block costs more
+// than the radix passes and range extraction it saves (measured on GB300:
+// 2.5 pairs per cell gain, 20 lose).
+bool use_hybrid(const grid_ctx *c, int64_t count, int64_t ncells)
+{
+    if (c->local_bits == -1) return false;
+    if (c->local_bits != 0) return true;
+    return (double)count <= LOCAL_PAIRS_PER_CELL * (double)std::max<int64_t>(ncells, 1);
+}
+
+// Local bits L of the hybrid placement for `count` pairs over `ncells` cells
+// with key_bits-bit keys: the radix passes sort the bits from L up and one
+// block per bucket of 2^L cells sorts the rest.  L_hi is the largest L whose
+// mean bucket (count * 2^L / ncells pairs) stays within half of what one
+// block places at once; the passes are the fewest that bring the remaining
+// bits down to L_hi with digits of at most rbits_max bits; L is then the
+// smallest value those passes reach with 8-bit digits (the fastest radix
+// kernels, and the smallest buckets, which matters on skewed scenes), but
+// not below L_hi - 3 (smaller buckets only add per-block work), or L_hi if
+// 8-bit digits cannot reach it.  One bucket of more pairs than a block holds
+// would leave a single block with the whole sort: at least one pass then.
+// A context's fixed local_bits (1..11) is used as it is.
+int choose_local_bits(const grid_ctx *c, int key_bits, int64_t count, int64_t ncells)
+{
+    if (key_bits <= 0) return 0;
+    if (c->local_bits > 0) return std::min(c->local_bits, key_bits);
+    const double per_cell = (double)count / (double)std::max<int64_t>(ncells, 1);
+    int l_hi = 0;
+    while (l_hi < gg::LOCAL_LMAX && per_cell * (double)(2ll << l_hi) <= 0.5 * gg::LOCAL_CAP) ++l_hi;
+    l_hi = std::min(l_hi, key_bits);
+    int passes = (key_bits - l_hi + c->rbits_max - 1) / c->rbits_max;
+    if (passes == 0 && count > gg::LOCAL_CAP) passes = 1;
+    const int l8 = std::max(0, key_bits - 8 * passes);
+    return l8 <= l_hi ? std::max(l8, l_hi - 3) : l_hi;
+}
+
+// RadixSort + RunLengthEncode / NonEmptyCells / ExclusiveSum, hybrid: the
+// radix passes order the pairs by the key bits from L up (the first pass
+// generating them when gen is set, else reading keys_in / vals_in), then
+// one block per bucket of 2^L cells sorts its pairs by cell in shared memory
+// and writes the bucket's part of cells (G) and refs.
+int sort_place(grid_ctx *c, int key_bits, int64_t ncells, unsigned count, bool gen, const ObjRec *recs,
+               int64_t nobj, const unsigned *tile_obj, unsigned res_x, unsigned res_y, const gg::MeshTab &mt,
+               const unsigned *keys_in, const unsigned *vals_in, unsigned *refs, unsigned *cells)
+{
+    const int L = choose_local_bits(c, key_bits, count, ncells);
+    const SortCfg sc = sort_cfg(key_bits, c->rbits_max, L, GG_FIRST_EXTRA);
+    const unsigned *K = keys_in, *V = vals_in;
+    if (sc.passes > 0 || gen) {
+        GG_TRY(ensure(c, c->keys_sorted, (size_t)count * sizeof(unsigned)));
+        GG_TRY(ensure(c, c->vals_sorted, (size_t)count * sizeof(unsigned)));
+        unsigned *k2 = (unsigned *)c->keys_sorted.ptr, *v2 = (unsigned *)c->vals_sorted.ptr;
+        if (sc.passes > 0) {
+            GG_TRY(sort_pairs(c, sc, count, gen, recs, nobj, tile_obj, res_x, res_y, mt, keys_in, vals_in, k2, v2,
+                              GG_FIRST_ANY != 0));
+        } else {   // one bucket holds every cell: the object-order pairs are its input
+            gg::EmitArgs ea{};
+            ea.recs = recs;
+            ea.tile_obj = tile_obj;
+            ea.mt = mt;
+            ea.res_x = res_x;
+            ea.res_y = res_y;
+            ea.count = count;
+            ea.C = k2;
+            ea.O = v2;
+            KernelScope ks(c, K_EMIT, 16.0 * nobj + 8.0 * count);
+            GG_CUDA(gg::launch_emit(ea, c->stream));
+        }
+        K = k2;
+        V = v2;
+    }
+    gg::LocalArgs la{};
+    la.keys = K;
+    la.vals = V;
+    la.count = count;
+    la.ncells = (unsigned long long)ncells;
+    la.lbits = L;
+    la.nbuckets = (unsigned)(((unsigned long long)ncells - 1ull) >> L) + 1u;
+    // groups open at bucket 0, at every bmax-th bucket, where the pair count
+    // crosses a multiple of group_pairs, and around each bucket of more than
+    // LOCAL_CAP - group_pairs (>= group_pairs) pairs; each holds a bucket
+    const unsigned long long bmax = (1ull << gg::LOCAL_LMAX) >> L;
+    const unsigned long long per = gg::LOCAL_GROUP_PAIRS;
+    la.max_groups = (unsigned)std::min<unsigned long long>(
+        la.nbuckets, 2ull + la.nbuckets / bmax + 3ull * ((unsigned long long)count / per + 1ull));
+    la.group_pairs = gg::LOCAL_GROUP_PAIRS;
+    GG_TRY(ensure(c, c->bstarts, (size_t)(la.nbuckets + 1) * sizeof(unsigned)));
+    GG_TRY(ensure(c, c->bgroups, (size_t)la.max_groups * sizeof(unsigned)));
+    la.starts = (unsigned *)c->bstarts.ptr;
+    la.groups = (unsigned *)c->bgroups.ptr;
+    la.refs = refs;
+    la.G = cells;
+    la.ctl = c->d_ctl;
+    GG_CUDA(cudaMemsetAsync(&c->d_ctl->tickets[2], 0, sizeof(unsigned), c->stream));
+    {
+        KernelScope ks(c, K_BSPLIT, 4.0 * (la.nbuckets + 1));
+        GG_CUDA(gg::launch_bucket_split(la, c->stream));
+    }
+    KernelScope ks(c, K_LOCAL, 12.0 * count + 4.0 * ncells);
+    GG_CUDA(gg::launch_local_sort(la, c->stream));
+    return GRID_OK;
+}
+
+// RadixSort over every key bit, then RunLengthEncode / NonEmptyCells /
+// ExclusiveSum by range extraction (the paper's chain): the placement a
+// hybrid build falls back to when a group of buckets is too large for one
+// block (ERR_LOCAL_FALLBACK).  Same arguments as sort_place.
+int place_lsd(grid_ctx *c, int key_bits, int64_t ncells, unsigned count, bool gen, const ObjRec *recs,
+              int64_t nobj, const unsigned *tile_obj, unsigned res_x, unsigned res_y, const gg::MeshTab &mt,
+              const unsigned *keys_in, const unsigned *vals_in, unsigned *refs, unsigned *cells)
+{
+    const SortCfg sc = sort_cfg(key_bits, c->rbits_max);
+    GG_TRY(ensure(c, c->keys_sorted, (size_t)count * sizeof(unsigned)));
+    unsigned *keys = (unsigned *)c->keys_sorted.ptr;
+    if (sc.passes > 0) {
+        GG_TRY(sort_pairs(c, sc, count, gen, recs, nobj, tile_obj, res_x, res_y, mt, keys_in, vals_in, keys, refs));
+    } else if (gen) {
+        gg::EmitArgs ea{};
+        ea.recs = recs;
+        ea.tile_obj = tile_obj;
+        ea.mt = mt;
+        ea.res_x = res_x;
+        ea.res_y = res_y;
+        ea.count = count;
+        ea.C = keys;
+        ea.O = refs;
+        KernelScope ks(c, K_EMIT, 16.0 * nobj + 8.0 * count);
+        GG_CUDA(gg::launch_emit(ea, c->stream));
+    } else {   // one cell: every key is the same
+        GG_CUDA(cudaMemcpyAsync(keys, keys_in, (size_t)count * 4, cudaMemcpyDeviceToDevice, c->stream));
+        GG_CUDA(cudaMemcpyAsync(refs, vals_in, (size_t)count * 4, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return extract_ranges(c, keys, count, ncells, cells);
+}
+
+// After a hybrid placement and read_ctl: if a group asked for it, clears the
+// request and places the build again with place_lsd.  *redone tells whether
+// it did (the caller then reads the control block again).
+int fallback_if_asked(grid_ctx *c, bool *redone, int key_bits, int64_t ncells, unsigned count, bool gen,
+                      const ObjRec *recs, int64_t nobj, const unsigned *tile_obj, unsigned res_x, unsigned res_y,
+                      const gg::MeshTab &mt, const unsigned *keys_in, const unsigned *vals_in, unsigned *refs,
+                      unsigned *cells)
+{
+    *redone = false;
+    if (!(c->h_ctl->err & gg::ERR_LOCAL_FALLBACK)) return GRID_OK;
+    c->h_ctl->err &= ~gg::ERR_LOCAL_FALLBACK;
+    GG_CUDA(cudaMemcpyAsync(&c->d_ctl->err, &c->h_ctl->err, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
+    c->fallbacks += 1;
+    *redone = true;
+    return place_lsd(c, key_bits, ncells, count, gen, recs, nobj, tile_obj, res_x, res_y, mt, keys_in, vals_in,
+                     refs, cells);
 }
 
 // Output placement for build_core: returns device pointers for cells
@@ -515,6 +710,30 @@ int cull_pairs(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
     GG_TRY(read_ctl(c));
     GG_TRY(ctl_error(c->h_ctl->err));
     *nkept = (int64_t)c->h_ctl->nkept;
+    return GRID_OK;
+}
+
+// The object-order pairs (C, O) written to device memory by the emit kernel
+// (GRID_PAIRS_EMIT) or one thread per object (GRID_PAIRS_PER_OBJECT).
+int pairs_in_memory(grid_ctx *c, const ObjRec *recs, int64_t n, const unsigned *tile_obj, const grid_info &I,
+                    unsigned count, unsigned *C, unsigned *O)
+{
+    if (c->pair_gen == GRID_PAIRS_PER_OBJECT) {
+        KernelScope ks(c, K_PER_OBJECT, 16.0 * n + 8.0 * count);
+        GG_CUDA(gg::launch_make_pairs_per_object(recs, n, (unsigned)I.res[0], (unsigned)I.res[1], count, C, O,
+                                                 c->d_ctl, c->stream));
+        return GRID_OK;
+    }
+    gg::EmitArgs ea{};
+    ea.recs = recs;
+    ea.tile_obj = tile_obj;
+    ea.res_x = (unsigned)I.res[0];
+    ea.res_y = (unsigned)I.res[1];
+    ea.count = count;
+    ea.C = C;
+    ea.O = O;
+    KernelScope ks(c, K_EMIT, 16.0 * n + 8.0 * count);
+    GG_CUDA(gg::launch_emit(ea, c->stream));
     return GRID_OK;
 }
 
@@ -588,7 +807,23 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
         GG_TRY(cull_pairs(c, verts, nverts, tris, I, (const ObjRec *)c->recs.ptr, n, NO, C, O, &NK));
         I.nrefs = NK;
         GG_TRY(out.alloc(c, I.ncells + 1, NK, &cells, &refs));
-        if (NK > 0) {
+        if (NK > 0 && use_hybrid(c, NK, I.ncells)) {
+            GG_TRY(sort_place(c, I.key_bits, I.ncells, (unsigned)NK, false, nullptr, 0, nullptr, 0, 0, gg::MeshTab{},
+                              C, O, refs, cells));
+            GG_TRY(out.refs_ready(c, refs, NK));
+            GG_TRY(read_ctl(c));
+            GG_TRY(ctl_error(c->h_ctl->err));
+            bool redone = false;
+            GG_TRY(fallback_if_asked(c, &redone, I.key_bits, I.ncells, (unsigned)NK, false, nullptr, 0, nullptr, 0, 0,
+                                     gg::MeshTab{}, C, O, refs, cells));
+            if (redone) {
+                GG_TRY(out.refs_ready(c, refs, NK));
+                GG_TRY(read_ctl(c));
+            }
+            GG_TRY(ctl_error(c->h_ctl->err));
+            if (info) *info = I;
+            return GRID_OK;
+        } else if (NK > 0) {
             const unsigned kc = (unsigned)NK;
             const SortCfg sc = sort_cfg(I.key_bits, c->rbits_max);
             const unsigned *keys = C;
@@ -623,9 +858,38 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
             KernelScope ks(c, K_TILES, 4.0 * (ntiles + 1));
             GG_CUDA(gg::launch_tile_search(recs, n, gg::PAIR_TILE, ntiles, tile_obj, c->stream));
         }
+        const bool in_memory = c->pair_gen == GRID_PAIRS_EMIT || c->pair_gen == GRID_PAIRS_PER_OBJECT;
+        if (use_hybrid(c, count, I.ncells)) {
+            // hybrid: radix passes over the high key bits, then the per-bucket
+            // counting sort writes refs and cells
+            unsigned *C = nullptr, *O = nullptr;
+            if (in_memory) {
+                GG_TRY(ensure(c, c->pairs_C, (size_t)count * sizeof(unsigned)));
+                GG_TRY(ensure(c, c->pairs_O, (size_t)count * sizeof(unsigned)));
+                C = (unsigned *)c->pairs_C.ptr;
+                O = (unsigned *)c->pairs_O.ptr;
+                GG_TRY(pairs_in_memory(c, recs, n, tile_obj, I, count, C, O));
+            }
+            const unsigned rx = (unsigned)I.res[0], ry = (unsigned)I.res[1];
+            GG_TRY(sort_place(c, I.key_bits, I.ncells, count, !in_memory, recs, n, tile_obj, rx, ry, gg::MeshTab{}, C,
+                              O, refs, cells));
+            GG_TRY(out.refs_ready(c, refs, count));
+            GG_TRY(read_ctl(c));
+            GG_TRY(ctl_error(c->h_ctl->err));
+            bool redone = false;
+            GG_TRY(fallback_if_asked(c, &redone, I.key_bits, I.ncells, count, !in_memory, recs, n, tile_obj, rx, ry,
+                                     gg::MeshTab{}, C, O, refs, cells));
+            if (redone) {
+                GG_TRY(out.refs_ready(c, refs, count));
+                GG_TRY(read_ctl(c));
+                GG_TRY(ctl_error(c->h_ctl->err));
+            }
+            if (info) *info = I;
+            return GRID_OK;
+        }
         GG_TRY(ensure(c, c->keys_sorted, (size_t)count * sizeof(unsigned)));
         unsigned *keys_sorted = (unsigned *)c->keys_sorted.ptr;
-        if (sc.passes == 0 || c->pair_gen == GRID_PAIRS_EMIT || c->pair_gen == GRID_PAIRS_PER_OBJECT) {
+        if (sc.passes == 0 || in_memory) {
             // object-order (C, O) in device memory: straight into the outputs
             // when there is nothing to sort, else into scratch for the sort
             unsigned *C = keys_sorted, *O = refs;
@@ -635,22 +899,7 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
                 C = (unsigned *)c->pairs_C.ptr;
                 O = (unsigned *)c->pairs_O.ptr;
             }
-            if (c->pair_gen == GRID_PAIRS_PER_OBJECT) {
-                KernelScope ks(c, K_PER_OBJECT, 16.0 * n + 8.0 * count);
-                GG_CUDA(gg::launch_make_pairs_per_object(recs, n, (unsigned)I.res[0], (unsigned)I.res[1], count, C,
-                                                         O, c->d_ctl, c->stream));
-            } else {
-                gg::EmitArgs ea{};
-                ea.recs = recs;
-                ea.tile_obj = tile_obj;
-                ea.res_x = (unsigned)I.res[0];
-                ea.res_y = (unsigned)I.res[1];
-                ea.count = count;
-                ea.C = C;
-                ea.O = O;
-                KernelScope ks(c, K_EMIT, 16.0 * n + 8.0 * count);
-                GG_CUDA(gg::launch_emit(ea, c->stream));
-            }
+            GG_TRY(pairs_in_memory(c, recs, n, tile_obj, I, count, C, O));
             if (sc.passes > 0)
                 GG_TRY(sort_pairs(c, sc, count, false, nullptr, 0, nullptr, 0, 0, gg::MeshTab{}, C, O, keys_sorted,
                                   refs));
@@ -785,6 +1034,11 @@ int grid_ctx_create(int device, const grid_opts *opts, grid_ctx **out)
         return GRID_EINVAL;
     }
     c->shape = c->opts.tile_shape;
+    if (c->opts.local_bits < -2 || c->opts.local_bits > gg::LOCAL_LMAX) {
+        delete c;
+        return GRID_EINVAL;
+    }
+    c->local_bits = c->opts.local_bits;
     int rc = GRID_OK;
     do {
         if ((rc = cuda_err(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device)))) break;
@@ -822,6 +1076,7 @@ void grid_ctx_destroy(grid_ctx *c)
         DeviceGuard g(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
         Scratch *all[] = {&c->recs, &c->k2status, &c->tile_obj, &c->splits, &c->keys_sorted, &c->keys[0],
+                          &c->vals_sorted, &c->bstarts, &c->bgroups,
                           &c->vals[0], &c->intra, &c->gpref, &c->gstatus, &c->in_verts, &c->in_tris,
                           &c->out_cells, &c->out_refs, &c->b_desc, &c->b_base, &c->b_state, &c->b_pairbase,
                           &c->b_cellsoff, &c->b_G, &c->pairs_C, &c->pairs_O, &c->cstatus};
@@ -855,6 +1110,21 @@ int grid_ctx_mem_in_use(grid_ctx *c, int64_t *bytes)
 {
     if (!c || !bytes) return GRID_EINVAL;
     *bytes = c->in_use.load();
+    return GRID_OK;
+}
+
+int grid_ctx_sort_plan(grid_ctx *c, int32_t key_bits, int64_t count, int64_t ncells, int32_t *local_bits,
+                       int32_t *passes)
+{
+    if (!c || !local_bits || key_bits < 0 || key_bits > 31 || count < 0 || ncells < 1) return GRID_EINVAL;
+    if (!use_hybrid(c, count, ncells)) {
+        *local_bits = -1;
+        if (passes) *passes = sort_cfg(key_bits, c->rbits_max).passes;
+        return GRID_OK;
+    }
+    const int L = choose_local_bits(c, key_bits, count, ncells);
+    *local_bits = L;
+    if (passes) *passes = sort_cfg(key_bits, c->rbits_max, L).passes;
     return GRID_OK;
 }
 
@@ -916,7 +1186,7 @@ int grid_ctx_autotune(grid_ctx *c, const float *verts, int64_t nverts, const int
     if (reps <= 0) reps = 3;
     if (reps > 64) return GRID_EINVAL;
     DeviceGuard g(c->device);
-    const int saved_rbits = c->rbits_max, saved_pg = c->pair_gen, saved_shape = c->shape;
+    const int saved_rbits = c->rbits_max, saved_pg = c->pair_gen, saved_shape = c->shape, saved_lb = c->local_bits;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -981,23 +1251,163 @@ int grid_ctx_autotune(grid_ctx *c, const float *verts, int64_t nverts, const int
             }
         }
     }
+    // then the other way to finish the sort and the range steps: radix
+    // passes over every key bit and extraction when the context uses the
+    // per-bucket counting sort, and the automatic hybrid otherwise
+    int best_lb = saved_lb;
+    if (rc == GRID_OK) {
+        c->shape = best_shape;
+        // the context's own choice for this mesh (its pair and cell counts
+        // come from one more build), then the other one: radix passes over
+        // every key bit if it chose the hybrid, the hybrid if it did not
+        grid_info probe{};
+        grid_buf cells{}, refs{};
+        PoolOut po(&cells, &refs);
+        c->local_bits = saved_lb;
+        rc = build_core(c, verts, nverts, tris, n, lambda, &probe, po);
+        grid_buf_free(c, &cells);
+        grid_buf_free(c, &refs);
+        c->local_bits = use_hybrid(c, probe.nrefs, probe.ncells) ? -1 : -2;
+        double med = 0.0;
+        if (rc == GRID_OK) rc = time_setting(&med);
+        if (rc == GRID_OK) {
+            if (times) times[9] = med;
+            if (med < best) {
+                best = med;
+                best_lb = c->local_bits;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != GRID_OK) {
         c->rbits_max = saved_rbits;
         c->pair_gen = saved_pg;
         c->shape = saved_shape;
+        c->local_bits = saved_lb;
         return rc;
     }
     c->rbits_max = best_rbits;
     c->pair_gen = best_pg;
     c->shape = best_shape;
+    c->local_bits = best_lb;
     if (chosen) {
         std::memset(chosen, 0, sizeof(*chosen));
         chosen->radix_bits = best_rbits;
         chosen->pair_gen = best_pg;
         chosen->cull = c->cull ? 1 : 0;
         chosen->tile_shape = best_shape;
+        chosen->local_bits = best_lb;
+    }
+    return GRID_OK;
+}
+
+int grid_ctx_autotune_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, int32_t reps,
+                              grid_opts *chosen, double *times)
+{
+    if (!c || !meshes || nmeshes < 1) return GRID_EINVAL;
+    if (reps <= 0) reps = 3;
+    if (reps > 64) return GRID_EINVAL;
+    DeviceGuard g(c->device);
+    const int saved_rbits = c->rbits_max, saved_shape = c->shape, saved_lb = c->local_bits;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return GRID_ECUDA;
+    }
+    std::vector<grid_info> infos((size_t)nmeshes);
+    std::vector<int64_t> coff((size_t)nmeshes), roff((size_t)nmeshes);
+    // median ms of `reps` batched builds with the context's current setting,
+    // after one warm-up build
+    auto time_setting = [&](double *med) -> int {
+        std::vector<float> ms;
+        for (int r = 0; r <= reps; ++r) {
+            grid_buf cells{}, refs{};
+            cudaEventRecord(e0, c->stream);
+            int rc = grid_build_batched(c, meshes, nmeshes, &cells, &refs, infos.data(), coff.data(), roff.data());
+            cudaEventRecord(e1, c->stream);
+            grid_buf_free(c, &cells);
+            grid_buf_free(c, &refs);
+            if (rc != GRID_OK) return rc;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                return GRID_ECUDA;
+            }
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (r > 0) ms.push_back(t);
+        }
+        std::sort(ms.begin(), ms.end());
+        *med = ms[ms.size() / 2];
+        return GRID_OK;
+    };
+    double best = -1.0;
+    int best_rbits = saved_rbits, best_shape = saved_shape, best_lb = saved_lb, rc = GRID_OK;
+    grid_buf probe_cells{}, probe_refs{};
+    for (int rb = 8; rb <= 11 && rc == GRID_OK; ++rb) {
+        c->rbits_max = rb;
+        double med = 0.0;
+        if ((rc = time_setting(&med)) != GRID_OK) break;
+        if (times) times[rb - 8] = med;
+        if (best < 0.0 || med < best) {
+            best = med;
+            best_rbits = rb;
+        }
+    }
+    if (rc == GRID_OK) {   // the other block shape with the winning digit width
+        c->rbits_max = best_rbits;
+        c->shape = saved_shape == gg::SHAPE_MAIN ? gg::SHAPE_ALT : gg::SHAPE_MAIN;
+        double med = 0.0;
+        if ((rc = time_setting(&med)) == GRID_OK) {
+            if (times) times[4] = med;
+            if (med < best) {
+                best = med;
+                best_shape = c->shape;
+            }
+        }
+    }
+    if (rc == GRID_OK) {   // the other way to finish the sort and the range steps (as grid_ctx_autotune)
+        c->shape = best_shape;
+        c->local_bits = saved_lb;
+        rc = grid_build_batched(c, meshes, nmeshes, &probe_cells, &probe_refs, infos.data(), coff.data(),
+                                roff.data());
+        int64_t np = 0, nc = 0;
+        for (int m = 0; m < nmeshes; ++m) {
+            np += infos[m].nrefs;
+            nc += infos[m].ncells;
+        }
+        grid_buf_free(c, &probe_cells);
+        grid_buf_free(c, &probe_refs);
+        c->local_bits = use_hybrid(c, np, nc) ? -1 : -2;
+        double med = 0.0;
+        if (rc == GRID_OK) rc = time_setting(&med);
+        if (rc == GRID_OK) {
+            if (times) times[5] = med;
+            if (med < best) {
+                best = med;
+                best_lb = c->local_bits;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GRID_OK) {
+        c->rbits_max = saved_rbits;
+        c->shape = saved_shape;
+        c->local_bits = saved_lb;
+        return rc;
+    }
+    c->rbits_max = best_rbits;
+    c->shape = best_shape;
+    c->local_bits = best_lb;
+    if (chosen) {
+        std::memset(chosen, 0, sizeof(*chosen));
+        chosen->radix_bits = best_rbits;
+        chosen->pair_gen = GRID_PAIRS_FUSED;
+        chosen->cull = c->cull ? 1 : 0;
+        chosen->tile_shape = best_shape;
+        chosen->local_bits = best_lb;
     }
     return GRID_OK;
 }
@@ -1191,7 +1601,10 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
             int key_bits = 0;
             for (unsigned long long v = (unsigned long long)(ncells_all - 1); v; v >>= 1) ++key_bits;
             const SortCfg sc = sort_cfg(key_bits, c->rbits_max);
-            if (sc.passes == 0) {
+            if (use_hybrid(c, count, ncells_all)) {
+                GG_TRY(sort_place(c, key_bits, ncells_all, count, true, recs, ntot, tile_obj, 0, 0, mt, nullptr, nullptr,
+                                  (unsigned *)pr, G));
+            } else if (sc.passes == 0) {
                 gg::EmitArgs ea{};
                 ea.recs = recs;
                 ea.tile_obj = tile_obj;
@@ -1205,21 +1618,37 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
                 GG_TRY(sort_pairs(c, sc, count, true, recs, ntot, tile_obj, 0, 0, mt, nullptr, nullptr, keys_sorted,
                                   (unsigned *)pr));
             }
-            GG_TRY(extract_ranges(c, keys_sorted, count, ncells_all, G));
+            if (!use_hybrid(c, count, ncells_all)) GG_TRY(extract_ranges(c, keys_sorted, count, ncells_all, G));
         } else {
             GG_CUDA(cudaMemsetAsync(G, 0, (size_t)(ncells_all + 1) * sizeof(unsigned), c->stream));
         }
         GG_CUDA(cudaMemcpyAsync(c->b_cellsoff.ptr, cells_off, sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice,
                                 c->stream));
         GG_CUDA(cudaMemcpyAsync(pair_base_d, pair_base, sizeof(unsigned) * nm, cudaMemcpyHostToDevice, c->stream));
-        {
+        auto localize = [&]() -> int {
             KernelScope ks(c, K_LOCALIZE, 8.0 * ncells_out);
             GG_CUDA(gg::launch_localize(G, (const long long *)c->b_cellsoff.ptr, pair_base_d, nm, ncells_out,
                                         (unsigned *)pc, c->stream));
-        }
+            return GRID_OK;
+        };
+        GG_TRY(localize());
         GG_TRY(read_ctl(c));
         c->stage_busy = false;
-        return ctl_error(c->h_ctl->err);
+        GG_TRY(ctl_error(c->h_ctl->err));
+        if (NO > 0 && use_hybrid(c, NO, ncells_all)) {
+            int key_bits = 0;
+            for (unsigned long long v = (unsigned long long)(ncells_all - 1); v; v >>= 1) ++key_bits;
+            bool redone = false;
+            GG_TRY(fallback_if_asked(c, &redone, key_bits, ncells_all, (unsigned)NO, true, (const ObjRec *)c->recs.ptr,
+                                     ntot, (const unsigned *)c->tile_obj.ptr, 0, 0, mt, nullptr, nullptr,
+                                     (unsigned *)pr, G));
+            if (redone) {
+                GG_TRY(localize());
+                GG_TRY(read_ctl(c));
+                GG_TRY(ctl_error(c->h_ctl->err));
+            }
+        }
+        return GRID_OK;
     }();
     if (rc != GRID_OK) {
         grid_buf_free(c, out_cells);

@@ -163,17 +163,48 @@ def test_autotune_keeps_a_valid_setting_and_the_same_grid():
         r = c.autotune(v, t, s.lam, reps=2)
         assert r["radix_bits"] in (8, 9, 10, 11) and r["pair_gen"] in ("fused", "emit")
         assert r["tile_shape"] in ("256x12", "384x8")
+        assert r["local_bits"] in (0, -1, -2)
         tm = r["times_ms"]
-        assert len(tm) == 9 and all(ms > 0 for ms in tm.values())
-        combos = {k: ms for k, ms in tm.items() if k != "other_shape"}
+        assert len(tm) == 10 and all(ms > 0 for ms in tm.values())
+        combos = {k: ms for k, ms in tm.items() if k not in ("other_shape", "other_sort_end")}
         # the winning combination was found with the default shape; the other
-        # shape was then tried with it and kept only if faster
-        assert combos[(r["radix_bits"], r["pair_gen"])] == min(combos.values())
+        # shape was then tried with it and kept only if faster, then the
+        # other sort end with the kept shape
+        best = combos[(r["radix_bits"], r["pair_gen"])]
+        assert best == min(combos.values())
         if r["tile_shape"] == "384x8":
-            assert tm["other_shape"] < combos[(r["radix_bits"], r["pair_gen"])]
+            assert tm["other_shape"] < best
+            best = tm["other_shape"]
         else:
-            assert tm["other_shape"] >= combos[(r["radix_bits"], r["pair_gen"])]
+            assert tm["other_shape"] >= best
+        assert (tm["other_sort_end"] < best) == (r["local_bits"] != 0)
         after = c.build(v, t, s.lam)
         assert torch.equal(before.cells, after.cells) and torch.equal(before.refs, after.refs)
+    finally:
+        c.close()
+
+
+def test_autotune_batched_keeps_the_same_grids():
+    """The batch tuner times digit widths, the other block shape and the
+    other sort end on a batch, keeps a valid setting, and the batch's grids
+    (and each mesh's own build) stay the same."""
+    import paper_2403_10647_gb300 as pg
+    meshes = scenes.batched_meshes(12, scale=0.02)
+    args = [(dev(m.verts, torch.float32), dev(m.tris, torch.int32), m.lam) for m in meshes]
+    c = pg.Context(0)
+    try:
+        before = c.build_batched(args)
+        r = c.autotune_batched(args, reps=2)
+        assert r["radix_bits"] in (8, 9, 10, 11) and r["tile_shape"] in ("256x12", "384x8")
+        assert r["local_bits"] in (0, -1, -2)
+        tm = r["times_ms"]
+        assert len(tm) == 6 and all(ms > 0 for ms in tm.values())
+        widths = {k: ms for k, ms in tm.items() if isinstance(k, int)}
+        assert widths[r["radix_bits"]] == min(widths.values())
+        after = c.build_batched(args)
+        for a, b, m in zip(before, after, meshes):
+            assert torch.equal(a.cells, b.cells) and torch.equal(a.refs, b.refs)
+            o = oracle.build_grid(m.verts, m.tris, m.lam, method="counting")
+            assert np.array_equal(b.cells.cpu().numpy(), o.G) and np.array_equal(b.refs.cpu().numpy(), o.refs)
     finally:
         c.close()
