@@ -36,8 +36,15 @@ struct Ctl {
                                 // hybrid placement's bucket groups
     unsigned long long nkept;   // pairs the culling emit kept, written by its last tile
     unsigned pad[4];
+    // grid metadata M computed on the device from the bounds above (plan_kernel),
+    // for count/scan to read without a host round trip; the host checks it
+    // against its own plan from the same bounds
+    float plan_lo[3];
+    float plan_scale[3];
+    int plan_res[3];
+    unsigned plan_pad;
 };
-static_assert(sizeof(Ctl) == 96, "Ctl layout");
+static_assert(sizeof(Ctl) == 136, "Ctl layout");
 
 // One object's box in grid coordinates and its pair offset (grid_objrec).
 struct __align__(16) ObjRec {

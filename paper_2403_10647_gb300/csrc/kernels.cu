@@ -355,6 +355,14 @@ __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
     __shared__ unsigned long long s_excl;
     const int tid = threadIdx.x;
     if (tid == 0) s_tile = atomicAdd(&a.ctl->tickets[0], 1u);
+    if (a.device_plan) {   // the plan kernel's M, in place of the host's
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            a.lo[ax] = a.ctl->plan_lo[ax];
+            a.scale[ax] = a.ctl->plan_scale[ax];
+            a.res[ax] = a.ctl->plan_res[ax];
+        }
+    }
     __syncthreads();
     const unsigned tile = s_tile;
     const long long base = (long long)tile * T;
@@ -453,6 +461,57 @@ __global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// a1 on the device: grid metadata M from the bounds
+// ---------------------------------------------------------------------------
+
+__global__ void plan_kernel(Ctl *ctl, long long n, float lambda)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float lo[3], e[3];
+    int res[3] = {1, 1, 1};
+    float scale[3] = {0.0f, 0.0f, 0.0f};
+    const bool ok = ctl->err == 0u && n > 0;
+    int d = 0;
+    double vol = 1.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        // the bounds as the host reads them: a zero bound is +0.0
+        lo[a] = ok ? __fadd_rn(ordered_to_float(~ctl->lo_inv[a]), 0.0f) : 0.0f;
+        const float hi = ok ? __fadd_rn(ordered_to_float(ctl->hi_ord[a]), 0.0f) : 0.0f;
+        e[a] = __fsub_rn(hi, lo[a]);
+        if (ok && e[a] > 0.0f) {
+            ++d;
+            vol = __dmul_rn(vol, (double)e[a]);
+        }
+    }
+    if (d > 0) {
+        const double q = __ddiv_rn(__dmul_rn((double)lambda, (double)n), vol);
+        const double k = d == 3 ? cbrt(q) : (d == 2 ? __dsqrt_rn(q) : q);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!(e[a] > 0.0f)) continue;
+            double r = ceil(__dmul_rn((double)e[a], k));
+            if (!(r >= 1.0)) r = 1.0;
+            if (r > 65535.0) r = 65535.0;
+            res[a] = (int)r;
+            scale[a] = __fdiv_rn((float)res[a], e[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ctl->plan_lo[a] = lo[a];
+        ctl->plan_scale[a] = scale[a];
+        ctl->plan_res[a] = res[a];
+    }
+}
+
+cudaError_t launch_plan(Ctl *ctl, long long n, float lambda, cudaStream_t s)
+{
+    plan_kernel<<<1, 32, 0, s>>>(ctl, n, lambda);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -84,6 +84,7 @@ struct CountArgs {
     Ctl *ctl;
     MeshTab mt;                     // batched: per-object mesh (verts, tris, plan)
     unsigned *pair_base;            // batched: [nm] out, pair offset of each mesh's first object
+    bool device_plan;               // single mesh: take lo / scale / res from ctl->plan_* instead
 };
 
 struct EmitArgs {
@@ -195,6 +196,12 @@ cudaError_t launch_bounds_batched(const MeshTab &mt, long long ntot, unsigned *b
 cudaError_t launch_localize(const unsigned *G, const long long *cells_off, const unsigned *pair_base, int nm,
                             long long total, unsigned *out, cudaStream_t s);
 cudaError_t launch_count_scan(const CountArgs &a, cudaStream_t s);
+// Grid metadata M on the device (one thread): from ctl's bounds, n and
+// lambda, the resolution and scale of the density rule (the host plan's
+// formula and operation order; k's cube root is the device's cbrt), into
+// ctl->plan_*.  With an error bit already set it writes a harmless plan
+// (one cell, scale 0).
+cudaError_t launch_plan(Ctl *ctl, long long n, float lambda, cudaStream_t s);
 cudaError_t launch_tile_search(const ObjRec *recs, long long n, unsigned tile, unsigned ntiles,
                                unsigned *tile_obj, cudaStream_t s);
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t s);

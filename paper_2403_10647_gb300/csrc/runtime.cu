@@ -60,12 +60,12 @@ struct Scratch {
 
 enum KernelId {
     K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_LOCALIZE,
-    K_PER_OBJECT, K_CULL, K_BSPLIT, K_LOCAL, K_DOWN_ANY, K_NUM
+    K_PER_OBJECT, K_CULL, K_BSPLIT, K_LOCAL, K_DOWN_ANY, K_PLAN, K_NUM
 };
 const char *const kKernelNames[K_NUM] = {"bounds",  "count_scan",    "tile_search",   "emit",
                                          "upsweep_gen", "downsweep_gen", "upsweep", "downsweep",
                                          "extract_split", "extract",   "localize", "make_pairs_per_object",
-                                         "cull_emit", "bucket_split", "local_sort", "downsweep_first"};
+                                         "cull_emit", "bucket_split", "local_sort", "downsweep_first", "plan"};
 
 struct PendingTiming {
     int kid;
@@ -89,6 +89,7 @@ struct grid_ctx {
     bool cull = false;
     int local_bits = 0;          // grid_opts.local_bits
     int64_t fallbacks = 0;       // hybrid placements redone by radix passes over every key bit
+    int64_t plan_redos = 0;      // builds whose device M differed from the host's
 
     Ctl *d_ctl = nullptr;        // device control block
     Ctl *h_ctl = nullptr;        // pinned host mirror
@@ -754,44 +755,71 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
         if (info) *info = I;
         return GRID_OK;
     }
-    // a0: boxes + bounds
+    // a0: boxes + bounds, a1 on the device, a2 + a3 with the device's M: one
+    // host synchronisation for bounds, M and NO together
     GG_TRY(reset_ctl(c));
     {
         KernelScope ks(c, K_BOUNDS, 48.0 * n);
         GG_CUDA(gg::launch_bounds(verts, nverts, tris, n, c->d_ctl, c->nsm, c->stream));
     }
-    GG_TRY(read_ctl(c));
-    GG_TRY(ctl_error(c->h_ctl->err));
-    float lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = bound_lo(c->h_ctl->lo_inv[a]);
-        hi[a] = bound_hi(c->h_ctl->hi_ord[a]);
+    {
+        KernelScope ks(c, K_PLAN, 0.0);
+        GG_CUDA(gg::launch_plan(c->d_ctl, n, lambda, c->stream));
     }
-    // a1: M
-    GG_TRY(plan(lo, hi, n, lambda, &I));
-    // a2 + a3: CountCells + ExclusiveSum
     const int64_t ctiles = (n + gg::COUNT_TILE - 1) / gg::COUNT_TILE;
     GG_TRY(ensure(c, c->recs, (size_t)n * sizeof(ObjRec)));
     GG_TRY(ensure(c, c->k2status, (size_t)ctiles * 8));
-    GG_CUDA(cudaMemsetAsync(c->k2status.ptr, 0, (size_t)ctiles * 8, c->stream));
     gg::CountArgs ca{};
     ca.verts = verts;
     ca.nverts = nverts;
     ca.tris = tris;
     ca.n = n;
-    for (int a = 0; a < 3; ++a) {
-        ca.lo[a] = I.lo[a];
-        ca.scale[a] = I.scale[a];
-        ca.res[a] = I.res[a];
-    }
     ca.recs = (ObjRec *)c->recs.ptr;
     ca.status = (unsigned long long *)c->k2status.ptr;
     ca.ctl = c->d_ctl;
-    {
+    ca.device_plan = true;
+    auto count_scan = [&]() -> int {
+        GG_CUDA(cudaMemsetAsync(c->k2status.ptr, 0, (size_t)ctiles * 8, c->stream));
         KernelScope ks(c, K_COUNT, 64.0 * n);
         GG_CUDA(gg::launch_count_scan(ca, c->stream));
-    }
+        return GRID_OK;
+    };
+    GG_TRY(count_scan());
     GG_TRY(read_ctl(c));
+    if (c->h_ctl->err & (gg::ERR_BADINDEX | gg::ERR_NONFINITE)) return GRID_EINVAL;
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = bound_lo(c->h_ctl->lo_inv[a]);
+        hi[a] = bound_hi(c->h_ctl->hi_ord[a]);
+    }
+    // a1 on the host, the reference: the device's M must equal it (the two
+    // cube roots can differ by a rounding, which moves a resolution only if
+    // e * k lies within that of an integer); otherwise CountCells and
+    // ExclusiveSum run again with the host's M
+    GG_TRY(plan(lo, hi, n, lambda, &I));
+    bool same = true;
+    for (int a = 0; a < 3; ++a) {
+        unsigned sh, sd, lh, ld;
+        std::memcpy(&sh, &I.scale[a], 4);
+        std::memcpy(&sd, &c->h_ctl->plan_scale[a], 4);
+        std::memcpy(&lh, &I.lo[a], 4);
+        std::memcpy(&ld, &c->h_ctl->plan_lo[a], 4);
+        same = same && I.res[a] == c->h_ctl->plan_res[a] && sh == sd && lh == ld;
+    }
+    if (!same) {
+        c->plan_redos += 1;
+        ca.device_plan = false;
+        for (int a = 0; a < 3; ++a) {
+            ca.lo[a] = I.lo[a];
+            ca.scale[a] = I.scale[a];
+            ca.res[a] = I.res[a];
+        }
+        // the first count's tickets, NO and any overflow bit are stale
+        GG_CUDA(cudaMemsetAsync(&c->d_ctl->err, 0, sizeof(unsigned), c->stream));
+        GG_CUDA(cudaMemsetAsync(&c->d_ctl->tickets[0], 0, sizeof(unsigned), c->stream));
+        GG_TRY(count_scan());
+        GG_TRY(read_ctl(c));
+    }
     GG_TRY(ctl_error(c->h_ctl->err));
     const int64_t NO = (int64_t)c->h_ctl->nrefs;
     if (NO > kInt32Max) return GRID_EOVERFLOW;
@@ -1099,6 +1127,33 @@ void grid_ctx_destroy(grid_ctx *c)
     delete c;
 }
 
+int grid_ctx_get_opts(grid_ctx *c, grid_opts *out)
+{
+    if (!c || !out) return GRID_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->radix_bits = c->rbits_max;
+    out->pair_gen = c->pair_gen;
+    out->cull = c->cull ? 1 : 0;
+    out->tile_shape = c->shape;
+    out->local_bits = c->local_bits;
+    return GRID_OK;
+}
+
+int grid_ctx_set_opts(grid_ctx *c, const grid_opts *o)
+{
+    if (!c || !o) return GRID_EINVAL;
+    if ((o->radix_bits != 0 && (o->radix_bits < 8 || o->radix_bits > 11)) || o->pair_gen < GRID_PAIRS_FUSED ||
+        o->pair_gen > GRID_PAIRS_REGEN || (o->cull != 0 && o->cull != 1) || (o->tile_shape != 0 && o->tile_shape != 1) ||
+        o->local_bits < -2 || o->local_bits > gg::LOCAL_LMAX)
+        return GRID_EINVAL;
+    if (o->radix_bits) c->rbits_max = o->radix_bits;
+    c->pair_gen = o->pair_gen;
+    c->cull = o->cull == 1;
+    c->shape = o->tile_shape;
+    c->local_bits = o->local_bits;
+    return GRID_OK;
+}
+
 int grid_ctx_set_stream(grid_ctx *c, void *stream)
 {
     if (!c) return GRID_EINVAL;
@@ -1125,6 +1180,14 @@ int grid_ctx_sort_plan(grid_ctx *c, int32_t key_bits, int64_t count, int64_t nce
     const int L = choose_local_bits(c, key_bits, count, ncells);
     *local_bits = L;
     if (passes) *passes = sort_cfg(key_bits, c->rbits_max, L).passes;
+    return GRID_OK;
+}
+
+int grid_ctx_counters(grid_ctx *c, int64_t *fallbacks, int64_t *plan_redos)
+{
+    if (!c) return GRID_EINVAL;
+    if (fallbacks) *fallbacks = c->fallbacks;
+    if (plan_redos) *plan_redos = c->plan_redos;
     return GRID_OK;
 }
 

@@ -549,3 +549,60 @@ def test_bounded_wait_times_out_and_context_survives(ctx):
     s = scenes.uniform_soup(5_000, seed=99)
     g, o = build_both(ctx, s)
     assert_grid_equal(g, o, "after a timed-out wait")
+
+
+# ---- grid metadata computed on the device ---------------------------------------------
+
+def _plan_scene(lo, hi, n):
+    """n triangles whose union box is exactly [lo, hi]: the first spans it,
+    the others are points at lo."""
+    lo, hi = np.asarray(lo, np.float32), np.asarray(hi, np.float32)
+    v = np.stack([lo, hi, np.array([hi[0], lo[1], hi[2]], np.float32)])
+    tris = np.zeros((n, 3), np.int32)
+    tris[0] = (0, 1, 2)
+    return v, tris
+
+
+def test_device_plan_on_the_closed_form_cases(ctx):
+    """The build's grid metadata comes from the device (one host round trip
+    fewer) and is checked against the host's; on the hand-worked resolution
+    cases it must give exactly their res, scale and ncells."""
+    import _pins
+    before = ctx.counters()["plan_redos"]
+    for row in _pins.read_plan_cases():
+        lo, hi, n, lam = row[0:3], row[3:6], int(row[6]), row[7]
+        if n > 1_000_000 or row[14] > 10_000_000:
+            continue
+        v, t = _plan_scene(lo, hi, n)
+        g = ctx.build(dev(v, torch.float32), dev(t, torch.int32), lam)
+        assert tuple(g.info.res) == tuple(int(r) for r in row[8:11]), (row, tuple(g.info.res))
+        assert np.array_equal(np.array(g.info.scale, np.float32), np.array(row[11:14], np.float32)), row
+        assert g.info.ncells == int(row[14]), row
+    assert ctx.counters()["plan_redos"] == before   # exact cube roots: the device agrees
+
+
+def test_device_plan_random_bounds_match_oracle(ctx):
+    """Random bounds, triangle counts and densities: whatever the device's
+    cube root does, the build's metadata equals the oracle's bit for bit
+    (a disagreement re-runs CountCells with the host's plan)."""
+    g = np.random.Generator(np.random.Philox(23))
+    for k in range(200):
+        lo = (g.standard_normal(3) * 10.0 ** g.uniform(-2, 3)).astype(np.float32)
+        ext = (10.0 ** g.uniform(-2, 2, 3)).astype(np.float32)
+        if k % 9 == 0:
+            ext[g.integers(0, 3)] = 0.0
+        hi = (lo + ext).astype(np.float32)
+        n = int(g.integers(1, 64))
+        lam = float(np.float32(g.uniform(0.5, 2000.0)))
+        v, t = _plan_scene(lo, hi, n)
+        try:
+            p = oracle.plan(v.min(0), v.max(0), n, lam)
+        except oracle.OracleError:
+            continue
+        if p.ncells > 2_000_000:
+            continue
+        gr = ctx.build(dev(v, torch.float32), dev(t, torch.int32), lam)
+        assert tuple(gr.info.res) == tuple(p.res), (k, tuple(gr.info.res), p.res)
+        assert np.array_equal(np.array(gr.info.scale, np.float32).view(np.uint32), p.scale.view(np.uint32)), k
+        o = oracle.build_grid(v, t, lam, method="counting")
+        assert np.array_equal(host(gr.cells), o.G) and np.array_equal(host(gr.refs), o.refs), k
