@@ -253,14 +253,30 @@ def run_reference(args, rank, world):
     }))
 
 
-def bench_batched(ctx, scale: float, reps: int = 5):
+def bench_batched(scale: float, reps: int = 5):
     """Many meshes at once: one grid_build_batched against the same meshes
-    built back to back with grid_build, identical outputs checked."""
+    built back to back with grid_build, identical outputs checked.  The
+    context is first tuned on the batch (grid_ctx_autotune_batched: digit
+    width, block shape, sort end); both modes then run with its choice."""
     import torch
     import scenes
+    import paper_2403_10647_gb300 as pg
     meshes = scenes.batched_meshes(64, scale=scale)
     args = [(torch.from_numpy(s.verts).cuda(), torch.from_numpy(s.tris).cuda(), s.lam) for s in meshes]
     torch.cuda.synchronize()
+    ctx = pg.Context(0)
+    try:
+        tuned = ctx.autotune_batched(args, reps=3)
+        out = _bench_batched_timed(ctx, meshes, args, reps)
+    finally:
+        ctx.close()
+    out["autotune_choice"] = f"{tuned['radix_bits']}/{tuned['tile_shape']}/local_bits {tuned['local_bits']}"
+    out["autotune_ms"] = {str(k): round(v, 4) for k, v in tuned["times_ms"].items()}
+    return out
+
+
+def _bench_batched_timed(ctx, meshes, args, reps):
+    import torch
     batched = ctx.build_batched(args)
     for a, b in zip(args, batched):
         p = ctx.build(*a)
@@ -401,12 +417,21 @@ def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 2, max_batch: 
             srv.wait(tk).release()
         srv.stats(reset=True)
 
+        errors = []
+
         def collect(q):
+            # every ticket is released, failed ones too, so none keeps its
+            # admission reservation
             while True:
                 tk = q.get()
                 if tk is None:
                     return
-                srv.wait(tk).release()
+                try:
+                    srv.wait(tk).release()
+                except pg.GridError as e:
+                    if len(errors) < 4:
+                        errors.append(str(e))
+                    srv.release(tk)
 
         # (1) open loop
         q = queue.Queue()
@@ -433,8 +458,10 @@ def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 2, max_batch: 
                      "max_ms": st["max_us"] / 1e3, "p50_service_ms": st["p50_service_us"] / 1e3,
                      "builds_per_s": st["completed"] / wall, "batches": st["batches"],
                      "batched_requests": st["batched_requests"],
-                     "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9, "budget_gb": st["budget_bytes"] / 1e9}
+                     "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9, "budget_gb": st["budget_bytes"] / 1e9,
+                     "errors": list(errors)}
 
+        errors.clear()
         # (1b) open loop again, each request carrying its mesh's new vertex
         # positions from pinned host memory (grid_serve_submit's new_verts):
         # two frames per pool mesh, jittered once ahead of time; the request's
@@ -475,10 +502,12 @@ def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 2, max_batch: 
                              "builds_per_s": st["completed"] / wall,
                              "h2d_bytes_per_request": upd_bytes / max(st["completed"], 1),
                              "vertices": "new positions from pinned host memory per request (new_verts), "
-                                         "copied inside the latency; no device jitter"}
+                                         "copied inside the latency; no device jitter",
+                             "errors": list(errors)}
         del frames
 
         # (2) saturated, against back to back
+        errors.clear()
         nsat = min(1000, len(arr))
         reqs = [(int(m), int(sd)) for m, sd in zip(mesh[:nsat], seeds[:nsat])]
         pending = []
@@ -490,10 +519,12 @@ def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 2, max_batch: 
                     pending.append(tk)
                     break
                 if not pending:
-                    raise RuntimeError("one request exceeds the serving memory budget")
-                srv.wait(pending.pop(0)).release()
+                    raise RuntimeError("one request exceeds the serving memory budget: "
+                                       f"{srv.stats()['reserved_bytes']} of {srv.stats()['budget_bytes']} bytes "
+                                       "reserved with nothing pending")
+                _release(srv, pending.pop(0), errors)
         for tk in pending:
-            srv.wait(tk).release()
+            _release(srv, tk, errors)
         sat_wall = time.perf_counter() - t0
         st = srv.stats(reset=True)
         # spot-check identical outputs: every 50th request served vs plain
@@ -516,13 +547,26 @@ def bench_serve(ctx, seconds: float, rate: float, nworkers: int = 2, max_batch: 
                      "p99_ms": st["p99_us"] / 1e3, "batches": st["batches"],
                      "batched_requests": st["batched_requests"],
                      "back_to_back_builds_per_s": nsat / b2b_wall,
-                     "speedup": (nsat / sat_wall) / (nsat / b2b_wall), "outputs": "identical (every 50th checked)"}
+                     "speedup": (nsat / sat_wall) / (nsat / b2b_wall), "outputs": "identical (every 50th checked)",
+                     "failed": st["failed"], "errors": list(errors)}
     finally:
         srv.close()
     return {"pool_meshes": len(pool), "pool_tris": [int(min(s.n for s in pool)), int(max(s.n for s in pool))],
             "sigma": sigma, "workers": nworkers, "max_batch": max_batch, "batch_pairs": batch_pairs or (1 << 24),
             "small_lane": bool(small_lane),
             "open_loop": open_loop, "open_loop_host_updates": open_loop_updates, "saturated": saturated}
+
+
+def _release(srv, tk, errors):
+    """Waits for a served request and releases it, a failed one too (its
+    error message kept in `errors`)."""
+    import paper_2403_10647_gb300 as pg
+    try:
+        srv.wait(tk).release()
+    except pg.GridError as e:
+        if len(errors) < 4:
+            errors.append(str(e))
+        srv.release(tk)
 
 
 def run_ours(args, rank, world, local):
@@ -718,8 +762,8 @@ def run_ours(args, rank, world, local):
 
     extras = {}
     if not args.no_extras and world == 1:
-        extras["batched"] = bench_batched(ctx, 1.0)
-        extras["batched_small"] = bench_batched(ctx, 0.01, reps=20)
+        extras["batched"] = bench_batched(1.0)
+        extras["batched_small"] = bench_batched(0.01, reps=20)
         extras["serve"] = bench_serve(ctx, args.serve_seconds, args.serve_rate, radix_bits=args.radix_bits)
         extras["pair_gen_ablation"] = {args.workload: bench_pair_gen(scene)}
         extras["culling"] = {args.workload: bench_cull(scene)}

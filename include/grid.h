@@ -133,7 +133,17 @@ typedef struct {
  * a control block and the kernels' scratch.  opts may be NULL. */
 int grid_ctx_create(int device, const grid_opts *opts, grid_ctx **out);
 void grid_ctx_destroy(grid_ctx *ctx);
-/* Binds a cudaStream_t (passed as void*; NULL = the context's own stream). */
+/* The context's current settings (as grid_opts; radix_bits is the digit
+ * width in use), and a change of them for its later builds (radix_bits 0
+ * keeps the current width; values checked as grid_ctx_create does,
+ * GRID_EINVAL otherwise).  Not to be called while another thread builds
+ * with the context. */
+int grid_ctx_get_opts(grid_ctx *ctx, grid_opts *out);
+int grid_ctx_set_opts(grid_ctx *ctx, const grid_opts *opts);
+/* Binds a cudaStream_t (passed as void*).  NULL selects the context's own
+ * stream, a non-blocking stream: work on it is not ordered with the legacy
+ * default stream.  To run in order with work on the legacy default stream
+ * (stream handle 0 in most frameworks), pass cudaStreamLegacy, (void *)1. */
 int grid_ctx_set_stream(grid_ctx *ctx, void *stream);
 /* Device bytes currently held by the context's pool for outputs + scratch. */
 int grid_ctx_mem_in_use(grid_ctx *ctx, int64_t *bytes);
@@ -183,6 +193,15 @@ int grid_ctx_autotune(grid_ctx *ctx, const float *verts, int64_t nverts, const i
 int grid_ctx_sort_plan(grid_ctx *ctx, int32_t key_bits, int64_t count, int64_t ncells, int32_t *local_bits,
                        int32_t *passes);
 
+/* How often the context's builds took a slower way to the same grid since it
+ * was created (either pointer may be NULL): *fallbacks, hybrid placements
+ * redone by radix passes over every key bit (a cell beyond what a block
+ * sorts); *plan_redos, builds whose grid metadata computed on the device
+ * (to spare a host round trip between the bounds and CountCells) differed
+ * from the host's, so CountCells and ExclusiveSum ran again with the host's.
+ * Host only. */
+int grid_ctx_counters(grid_ctx *ctx, int64_t *fallbacks, int64_t *plan_redos);
+
 /* Turns event timing on (1) or off (0) and clears the statistics. */
 int grid_ctx_profile(grid_ctx *ctx, int enable);
 /* Synchronises the stream, resolves pending events and copies up to max
@@ -196,8 +215,10 @@ int grid_ctx_kernel_stats(grid_ctx *ctx, grid_kernel_stat *out, int max, int *co
  * (int32 vertex indices into verts[nverts][3], float32 xyz) at density
  * lambda (> 0, finite).  Outputs are allocated from the context's pool:
  * out_cells (int32 [ncells + 1]) and out_refs (int32 [nrefs]); info may be
- * NULL.  Synchronises the stream twice (scene bounds, then NO) to size the
- * outputs; the rest stays on the device.  n == 0 gives res (1,1,1),
+ * NULL.  Synchronises the stream once to size the outputs (the scene bounds,
+ * the grid metadata, computed on the device and checked against the host's
+ * from the same bounds, and NO come back together) and once at the end; the
+ * rest stays on the device.  n == 0 gives res (1,1,1),
  * cells = [0, 0], refs empty.  Errors: GRID_EINVAL (bad index, non-finite
  * coordinate, bad lambda, NULL pointer), GRID_EOVERFLOW, GRID_ENOMEM,
  * GRID_ETIMEOUT, GRID_ECUDA; outputs are left empty on error. */
@@ -368,11 +389,12 @@ int grid_jitter(grid_ctx *ctx, const float *verts, float *out, int64_t nverts, f
  * request: each request names a mesh and may carry the mesh's new vertex
  * positions, a jitter sigma and a seed; the server takes the new vertices
  * (or the registered ones), jitters them on the device if sigma > 0
- * (grid_jitter's definition) and builds their grid with Algorithm 1.  Worker threads, each with its own
- * stream and context, take queued requests in arrival order; a free worker
- * takes every queued request up to max_batch (and up to batch_pairs estimated
- * pairs) and builds them as one batch (grid_build_batched; grid_build for a
- * batch of one).  A request's result is bit-identical whichever batch,
+ * (grid_jitter's definition) and builds their grid with Algorithm 1.
+ * Worker threads, each with its own stream and context, take queued requests
+ * in arrival order (reserved workers, grid_serve_opts.small_workers, only
+ * those that fit a batch); a free worker takes every queued request up to
+ * max_batch (and up to batch_pairs estimated pairs) and builds them as one
+ * batch (grid_build_batched; grid_build for a batch of one).  A request's result is bit-identical whichever batch,
  * worker or stream builds it.
  *
  * Admission: every admitted request reserves an estimate of the device bytes
@@ -391,12 +413,20 @@ typedef struct {
     int64_t hbm_budget;   /* bytes that admitted requests may reserve; 0 -> 3/4 of the device's free
                              memory when the server is created */
     int32_t radix_bits;   /* as grid_opts.radix_bits; 0 -> default */
-    int32_t arrival_order; /* 0 (default): while every other worker runs a request too large to
-                             batch (estimated pairs above batch_pairs), a free worker takes the
-                             oldest requests that fit a batch first, so they do not queue behind
-                             the large ones; large requests keep their order among themselves and
-                             run as soon as no smaller one waits.  1: strict arrival order */
-    int32_t reserved[4];
+    int32_t arrival_order; /* without reserved workers (small_workers -1): 0 (default): while every
+                             other worker runs a request too large to batch (estimated pairs above
+                             batch_pairs), a free worker takes the oldest requests that fit a batch
+                             first, so they do not queue behind the large ones; large requests keep
+                             their order among themselves and run as soon as no smaller one waits.
+                             1: strict arrival order */
+    int32_t small_workers; /* workers besides nworkers reserved for requests that fit a batch, each
+                             on a stream of the highest priority, so small rebuilds neither queue
+                             behind large ones nor wait for their kernels' SMs: 0 -> 1, -1 -> none,
+                             1..8 */
+    int32_t tune_meshes;  /* 0 (default): grid_serve_register runs grid_ctx_autotune on the mesh
+                             and every rebuild of it alone (a batch of one) uses the kept
+                             setting; -1: the workers' default setting for every build */
+    int32_t reserved[2];
 } grid_serve_opts;
 
 typedef struct {
@@ -424,8 +454,10 @@ int grid_serve_create(int device, const grid_serve_opts *opts, grid_server **out
 void grid_serve_destroy(grid_server *srv);
 /* Copies a mesh (verts float32 [nverts][3], tris int32 [n][3]; host or device
  * pointers) into server-owned device memory, validates it with one build at
- * `lambda` and measures its pair and cell counts for admission.  Errors as
- * grid_build.  Synchronous; safe to call while requests run. */
+ * `lambda` and measures its pair and cell counts for admission; unless
+ * tune_meshes is -1, also times the autotuner's candidates on it (a few
+ * dozen builds).  Errors as grid_build.  Synchronous; safe to call while
+ * requests run. */
 int grid_serve_register(grid_server *srv, const float *verts, int64_t nverts, const int32_t *tris,
                         int64_t n, float lambda, int32_t *mesh_id);
 /* Queues a rebuild of mesh_id; *ticket identifies it.  The paper's case for

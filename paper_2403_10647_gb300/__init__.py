@@ -158,8 +158,12 @@ class Context:
 
     # -- helpers -------------------------------------------------------------
     def _bind_stream(self):
+        # torch's default stream is the legacy default stream (handle 0); it is
+        # bound as cudaStreamLegacy, as NULL would select the context's own
+        # non-blocking stream, which does not order with torch's work
         s = self._torch.cuda.current_stream(self.device)
-        check(self._lib.grid_ctx_set_stream(self._h, ctypes.c_void_p(s.cuda_stream)), "grid_ctx_set_stream")
+        h = s.cuda_stream or _lib.CUDA_STREAM_LEGACY
+        check(self._lib.grid_ctx_set_stream(self._h, ctypes.c_void_p(h)), "grid_ctx_set_stream")
 
     def _dev(self, t, dtype, cols=None):
         torch = self._torch
@@ -246,6 +250,13 @@ class Context:
         check(self._lib.grid_ctx_sort_plan(self._h, int(key_bits), int(count), int(ncells), ctypes.byref(lb),
                                            ctypes.byref(p)), "grid_ctx_sort_plan")
         return int(lb.value), int(p.value)
+
+    def counters(self) -> dict:
+        """{"fallbacks", "plan_redos"}: builds that took a slower way to the
+        same grid (see grid_ctx_counters)."""
+        fb, pr = ctypes.c_int64(), ctypes.c_int64()
+        check(self._lib.grid_ctx_counters(self._h, ctypes.byref(fb), ctypes.byref(pr)), "grid_ctx_counters")
+        return {"fallbacks": int(fb.value), "plan_redos": int(pr.value)}
 
     def profile(self, enable: bool = True) -> None:
         """Per-kernel CUDA-event timing on (clears the statistics)."""
@@ -475,7 +486,8 @@ class Server:
     become free; admission is by a device-memory budget."""
 
     def __init__(self, device: int = 0, nworkers: int = 0, max_batch: int = 0, batch_pairs: int = 0,
-                 hbm_budget: int = 0, radix_bits: int = 0, small_lane: bool = True):
+                 hbm_budget: int = 0, radix_bits: int = 0, small_lane: bool = True, small_workers: int = 0,
+                 tune_meshes: bool = True):
         import torch
         self._torch = torch
         self.device = torch.device("cuda", device)
@@ -484,6 +496,8 @@ class Server:
         o.nworkers, o.max_batch, o.batch_pairs = int(nworkers), int(max_batch), int(batch_pairs)
         o.hbm_budget, o.radix_bits = int(hbm_budget), int(radix_bits)
         o.arrival_order = 0 if small_lane else 1   # small lane: small requests pass large ones
+        o.small_workers = int(small_workers)       # 0: one reserved worker for small requests, -1: none
+        o.tune_meshes = 0 if tune_meshes else -1   # autotune each registered mesh for its rebuilds alone
         h = ctypes.c_void_p()
         check(self._lib.grid_serve_create(int(device), ctypes.byref(o), ctypes.byref(h)), "grid_serve_create")
         self._h = h

@@ -18,6 +18,9 @@ GRID_ECUDA = -6
 GRID_ENOSPC = -7
 GRID_ENOTREADY = -8
 GRID_ELIMIT = -9
+
+# cudaStreamLegacy: the handle of the legacy default stream (grid_ctx_set_stream)
+CUDA_STREAM_LEGACY = 1
 GRID_RES_MAX = 65535
 GRID_PAIRS_FUSED = 0
 GRID_PAIRS_EMIT = 1
@@ -62,7 +65,8 @@ class GridOpts(ctypes.Structure):
 
 class GridServeOpts(ctypes.Structure):
     _fields_ = [("nworkers", c_int32), ("max_batch", c_int32), ("batch_pairs", c_int64),
-                ("hbm_budget", c_int64), ("radix_bits", c_int32), ("arrival_order", c_int32), ("reserved", c_int32 * 4)]
+                ("hbm_budget", c_int64), ("radix_bits", c_int32), ("arrival_order", c_int32),
+                ("small_workers", c_int32), ("tune_meshes", c_int32), ("reserved", c_int32 * 2)]
 
 
 class GridServeStats(ctypes.Structure):
@@ -79,10 +83,13 @@ SIGNATURES = {
     "grid_ctx_create": (c_int32, [ctypes.c_int, P(GridOpts), P(c_void_p)]),
     "grid_ctx_destroy": (None, [c_void_p]),
     "grid_ctx_set_stream": (c_int32, [c_void_p, c_void_p]),
+    "grid_ctx_get_opts": (c_int32, [c_void_p, P(GridOpts)]),
+    "grid_ctx_set_opts": (c_int32, [c_void_p, P(GridOpts)]),
     "grid_ctx_mem_in_use": (c_int32, [c_void_p, P(c_int64)]),
     "grid_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "grid_version": (ctypes.c_char_p, []),
     "grid_ctx_profile": (c_int32, [c_void_p, ctypes.c_int]),
+    "grid_ctx_counters": (c_int32, [c_void_p, P(c_int64), P(c_int64)]),
     "grid_ctx_sort_plan": (c_int32, [c_void_p, c_int32, c_int64, c_int64, P(c_int32), P(c_int32)]),
     "grid_ctx_autotune": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_float, c_int32, P(GridOpts),
                                     P(ctypes.c_double)]),

@@ -49,6 +49,8 @@ struct Mesh {
     float lambda = 1.0f;
     int64_t est_pairs = 0;    // with headroom
     int64_t est_bytes = 0;    // admission estimate of one rebuild
+    bool tuned = false;       // opts holds the autotuner's setting for rebuilds of this mesh alone
+    grid_opts opts{};
 };
 
 // Output buffers of one build; freed when the last request viewing them is
@@ -84,6 +86,7 @@ struct Request {
 struct Worker {
     grid_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
+    bool small_only = false;    // takes only requests that fit a batch, on a high-priority stream
     float *jverts = nullptr;    // jittered vertices of the current batch
     size_t jbytes = 0;
     gg::JitterDesc *h_desc = nullptr, *d_desc = nullptr;   // [max_batch]
@@ -222,6 +225,7 @@ struct grid_server {
     bool stop = false;
     std::vector<std::unique_ptr<Worker>> workers;
     int busy_large = 0;         // workers running a request above batch_pairs
+    int n_small_workers = 0;    // workers reserved for requests that fit a batch
     std::mutex register_mu;
     // vertex updates: copied at submission into blocks of a server-owned
     // pool on a stream of their own, freed once their request is built
@@ -251,7 +255,8 @@ int cuda_rc(cudaError_t e)
 int64_t estimate_bytes(int64_t pairs, int64_t ncells, int64_t n, int64_t nverts)
 {
     return 4 * (ncells + 1) + 4 * pairs       // outputs
-         + 20 * pairs + 4 * (ncells + 1)      // keys + values x2, sorted keys, batch ranges
+         + 28 * pairs + 4 * (ncells + 1)      // keys + values x2, sorted keys and values, object-order
+                                              // pairs of the unfused modes, batch ranges
          + 16 * n + 12 * nverts + (1 << 20);  // records, jittered vertices, small tables
 }
 
@@ -323,8 +328,12 @@ void run_batch(Worker *w, const std::vector<Request *> &rs, const std::vector<Me
         auto out = std::make_shared<BatchOut>();
         out->ctx = w->ctx;
         Request *r = rs[0];
+        grid_opts keep{};
+        const bool tuned = ms[0].tuned && grid_ctx_get_opts(w->ctx, &keep) == GRID_OK &&
+                           grid_ctx_set_opts(w->ctx, &ms[0].opts) == GRID_OK;   // the mesh's own setting
         r->rc = grid_build(w->ctx, vsrc[0], ms[0].nverts, ms[0].tris, ms[0].n, ms[0].lambda, &out->cells,
                            &out->refs, &r->info);
+        if (tuned) grid_ctx_set_opts(w->ctx, &keep);
         if (r->rc == GRID_OK) {
             r->cells = out->cells;
             r->refs = out->refs;
@@ -386,17 +395,25 @@ void worker_main(grid_server *S, Worker *w)
         ms.clear();
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
-            if (S->stop) return;
             auto is_large = [&](uint64_t t) {
                 auto it = S->reqs.find(t);
                 return it != S->reqs.end() && S->meshes[it->second->mesh].est_pairs > S->opts.batch_pairs;
             };
-            // unless strict arrival order is asked for, the last worker not
-            // busy with a large request passes over large ones while a
-            // smaller one waits
-            bool skip_large = false;
-            if (!S->opts.arrival_order && S->busy_large >= (int)S->workers.size() - 1 && S->workers.size() > 1) {
+            auto has_work = [&] {
+                if (!w->small_only) return !S->queue.empty();
+                for (uint64_t t : S->queue)
+                    if (!is_large(t)) return true;
+                return false;
+            };
+            S->cv_work.wait(lk, [&] { return S->stop || has_work(); });
+            if (S->stop) return;
+            // a reserved worker passes over large requests; without reserved
+            // workers, unless strict arrival order is asked for, the last
+            // worker not busy with a large request passes over large ones
+            // while a smaller one waits
+            bool skip_large = w->small_only;
+            if (!skip_large && S->n_small_workers == 0 && !S->opts.arrival_order &&
+                S->busy_large >= (int)S->workers.size() - 1 && S->workers.size() > 1) {
                 for (uint64_t t : S->queue)
                     if (!is_large(t)) {
                         skip_large = true;
@@ -499,9 +516,11 @@ int grid_serve_create(int device, const grid_serve_opts *opts, grid_server **out
     grid_serve_opts o{};
     if (opts) o = *opts;
     if (o.nworkers < 0 || o.nworkers > 64 || o.max_batch < 0 || o.max_batch > 4096 || o.batch_pairs < 0 ||
-        o.hbm_budget < 0 || (o.arrival_order != 0 && o.arrival_order != 1))
+        o.hbm_budget < 0 || (o.arrival_order != 0 && o.arrival_order != 1) || o.small_workers < -1 ||
+        o.small_workers > 8 || (o.tune_meshes != 0 && o.tune_meshes != -1))
         return GRID_EINVAL;
     if (o.nworkers == 0) o.nworkers = 2;
+    if (o.small_workers == 0) o.small_workers = 1;
     if (o.max_batch == 0) o.max_batch = 32;
     if (o.batch_pairs == 0) o.batch_pairs = 1ll << 24;
     int prev = -1;
@@ -529,13 +548,21 @@ int grid_serve_create(int device, const grid_serve_opts *opts, grid_server **out
         uint64_t thr = UINT64_MAX;   // keep freed blocks for the next updates
         if (rc == GRID_OK) rc = cuda_rc(cudaMemPoolSetAttribute(S->upool, cudaMemPoolAttrReleaseThreshold, &thr));
     }
-    for (int i = 0; rc == GRID_OK && i < o.nworkers; ++i) {
+    const int nsmall = o.small_workers > 0 ? o.small_workers : 0;
+    S->n_small_workers = nsmall;
+    int prio_least = 0, prio_greatest = 0;
+    if (rc == GRID_OK) rc = cuda_rc(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+    for (int i = 0; rc == GRID_OK && i < o.nworkers + nsmall; ++i) {
         auto w = std::make_unique<Worker>();
+        w->small_only = i >= o.nworkers;
         grid_opts go{};
         go.radix_bits = o.radix_bits;
         void *p = nullptr;
         if ((rc = grid_ctx_create(device, &go, &w->ctx)) != GRID_OK) break;
-        if ((rc = cuda_rc(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking))) != GRID_OK) break;
+        // a reserved worker's kernels go ahead of the large rebuilds' when SMs free up
+        if ((rc = cuda_rc(cudaStreamCreateWithPriority(&w->stream, cudaStreamNonBlocking,
+                                                       w->small_only ? prio_greatest : prio_least))) != GRID_OK)
+            break;
         if ((rc = grid_ctx_set_stream(w->ctx, w->stream)) != GRID_OK) break;
         if ((rc = cuda_rc(cudaMallocHost(&p, sizeof(gg::JitterDesc) * o.max_batch))) != GRID_OK) break;
         w->h_desc = (gg::JitterDesc *)p;
@@ -630,6 +657,16 @@ int grid_serve_register(grid_server *S, const float *verts, int64_t nverts, cons
         const int64_t ncells = info.ncells + info.ncells / 10 + 64;
         m.est_pairs = pairs;
         m.est_bytes = estimate_bytes(pairs, ncells, n, nverts);
+        // the fastest setting for rebuilds of this mesh alone (every setting
+        // gives the same grid)
+        if (S->opts.tune_meshes == 0 && n > 0) {
+            grid_opts chosen{};
+            if ((rc = grid_ctx_autotune(probe, m.verts, nverts, m.tris, n, lambda, 2, &chosen, nullptr)) != GRID_OK)
+                break;
+            chosen.cull = 0;
+            m.opts = chosen;
+            m.tuned = true;
+        }
     } while (0);
     if (probe) grid_ctx_destroy(probe);
     if (rc == GRID_OK) {
@@ -716,7 +753,7 @@ int grid_serve_submit(grid_server *S, int32_t mesh_id, const float *new_verts, f
         S->queue.push_back(r->ticket);
         S->reqs.emplace(r->ticket, std::move(r));
     }
-    S->cv_work.notify_one();
+    S->cv_work.notify_all();   // a reserved worker may not take it: let every idle worker look
     return GRID_OK;
 }
 

@@ -56,6 +56,22 @@ def test_device_jitter_in_place(ctx):
     assert np.array_equal(host(ctx.jitter(dev(v, torch.float32), 0.02, 99)), want)
 
 
+def test_context_work_is_ordered_with_torch_default_stream(ctx):
+    """Calls made on torch's default stream (the legacy default stream) run in
+    its order: the jitter reads an input torch is still writing and torch's
+    copy back reads the jitter's output, with no synchronisation between
+    them (a context bound to its own non-blocking stream would race both)."""
+    nv = 3_000_000
+    torch.cuda.synchronize()
+    base = torch.arange(3 * nv, device="cuda", dtype=torch.float32).reshape(nv, 3)
+    v = base
+    for _ in range(20):   # a queue of torch work ahead of the jitter
+        v = v * 1.0 + 0.0
+    got = ctx.jitter(v, 0.01, 4242).cpu().numpy()
+    want = scenes.jitter_vertices(np.arange(3 * nv, dtype=np.float32).reshape(nv, 3), 0.01, 4242)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
 # ---- serving -----------------------------------------------------------------------
 
 def _pool():
@@ -495,3 +511,61 @@ def test_bad_vertex_updates(ctx, pool):
         assert srv.stats()["reserved_bytes"] == 0
     finally:
         srv.close()
+
+
+def test_reserved_worker_serves_small_requests_during_large_ones(ctx, pool):
+    """A worker reserved for requests that fit a batch (small_workers, on a
+    high-priority stream) builds a small request while the only general
+    worker is still on a large rebuild queued ahead of it; results match the
+    oracle, and without the reserved worker the small request waits."""
+    import paper_2403_10647_gb300 as pg
+    big = scenes.nonhomogeneous_soup(1_000_000, seed=308)
+    for reserved in (1, -1):
+        srv = pg.Server(0, nworkers=1, small_workers=reserved, small_lane=False)
+        try:
+            bid = srv.register(big.verts, big.tris, big.lam)
+            sid = srv.register(pool[0].verts, pool[0].tris, pool[0].lam)
+            srv.wait(srv.submit(bid, 0.0, 0), timeout=120).release()   # warm both paths
+            srv.wait(srv.submit(sid, 0.0, 0), timeout=120).release()
+            large = [srv.submit(bid, 0.01, 20 + k) for k in range(2)]
+            tk = srv.submit(sid, 0.01, 77)
+            r = srv.wait(tk, timeout=120)
+            first_done = srv.poll(large[0])
+            o = oracle.build_grid(scenes.jitter_vertices(pool[0].verts, 0.01, 77), pool[0].tris, pool[0].lam)
+            assert_same_as_oracle(r, o, f"small request, reserved {reserved}")
+            r.release()
+            if reserved == 1:
+                assert first_done is None, "the small request waited for the large rebuild ahead of it"
+            else:
+                assert first_done is not None, "without a reserved worker the small request ran early"
+            if first_done is not None:
+                first_done.release()
+            for t in large[1:] if first_done is not None else large:
+                srv.wait(t, timeout=120).release()
+        finally:
+            srv.close()
+
+
+def test_tuned_meshes_give_the_same_grids(ctx, pool):
+    """Rebuilds of a mesh alone run with the setting the autotuner chose for
+    it at registration (tune_meshes); every setting gives the same grid, so
+    a tuned and an untuned server return identical results, equal to the
+    oracle's."""
+    import paper_2403_10647_gb300 as pg
+    reqs = [(m, 0.01, 900 + m) for m in range(len(pool))] + [(4, 0.0, 0), (2, 0.02, 5)]
+    res = {}
+    for tune in (True, False):
+        srv = pg.Server(0, nworkers=1, max_batch=1, small_workers=-1, tune_meshes=tune)
+        try:
+            ids = [srv.register(s.verts, s.tris, s.lam) for s in pool]
+            res[tune] = _serve_all(srv, ids, reqs, serial=True)
+            assert srv.stats()["failed"] == 0
+        finally:
+            srv.close()
+    for k, (m, s, sd) in enumerate(reqs):
+        (ca, ra, ia), (cb, rb, ib) = res[True][k], res[False][k]
+        assert ia == ib and np.array_equal(ca, cb) and np.array_equal(ra, rb), f"request {k}"
+        sc = pool[m]
+        o = oracle.build_grid(scenes.jitter_vertices(sc.verts, s, sd), sc.tris, sc.lam,
+                              method="alg1" if sc.n < 50_000 else "counting")
+        assert np.array_equal(ca, o.G) and np.array_equal(ra, o.refs), f"request {k} vs oracle"
