@@ -1216,7 +1216,17 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_ker
             keys[i] = e < cnt ? __ldcs(a.keys_in + j0 + e) : 0u;
         }
     }
-    if (STABLE)
+    // IN_PAIR_KEEP: the input is ordered by key bits [keep_lo, shift), so a
+    // tile whose first and last elements share them holds one value of them
+    // and its equal digits may take any order; other tiles rank stably
+    bool stable = STABLE;
+    if (IN == IN_PAIR_KEEP && cnt > 0u) {
+        const unsigned k0 = __ldg(a.keys_in + j0), k1 = __ldg(a.keys_in + j0 + cnt - 1u);
+        const unsigned span = (unsigned)(sh - a.keep_lo);
+        const unsigned km = span >= 32u ? 0xFFFFFFFFu : (1u << span) - 1u;
+        stable = (((k0 ^ k1) >> a.keep_lo) & km) != 0u;
+    }
+    if (stable)
         for (int i = tid; i < BATCH * W * R; i += BLOCK) s_wmask[i] = 0u;
     __syncthreads();
 
@@ -1229,7 +1239,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_ker
     // shared-memory round trips overlap; the reservations are issued in
     // item order, which keeps the ranks stable.
     unsigned ranks[ITEMS / 2];   // 16-bit ranks, two per register
-    if (!STABLE) {
+    if (!stable) {
         // runs of equal digits in consecutive lanes (pairs of one object often
         // share the high digits): the run's first lane reserves the run's
         // slots with one shared atomic and the others count from it
@@ -1259,6 +1269,7 @@ __global__ void __launch_bounds__(BLOCK, pass_min_blocks<BLOCK>()) downsweep_ker
     }
 #pragma unroll
     for (int ib = 0; ib < (STABLE ? ITEMS : 0); ib += BATCH) {
+        if (!stable) break;
         unsigned d[BATCH], peers[BATCH], old[BATCH];
         bool ok[BATCH];
 #pragma unroll
@@ -1588,48 +1599,115 @@ __device__ __forceinline__ unsigned run_end(const unsigned *bits, unsigned j, un
     return x ? min((w << 5) + (unsigned)__ffs(x) - 1u, n) : n;
 }
 
+// The run [lo, hi) of s_o holding position j: its ends are found in j's bit
+// word or its two neighbours (a run longer than 32 searches on).
+__device__ __forceinline__ void run_bounds(const unsigned *bits, unsigned j, unsigned n, unsigned nw, unsigned &lo,
+                                           unsigned &hi)
+{
+    const unsigned w = j >> 5, bp = j & 31u;
+    const unsigned x0 = bits[w];
+    const unsigned xm = w > 0u ? bits[w - 1u] : 0u;
+    const unsigned xp = w + 1u < nw ? bits[w + 1u] : 0u;
+    const unsigned below = x0 & (0xFFFFFFFFu >> (31u - bp));
+    const unsigned above = bp == 31u ? 0u : x0 & (0xFFFFFFFEu << bp);
+    if (below)
+        lo = (w << 5) + 31u - __clz(below);
+    else if (xm)
+        lo = ((w - 1u) << 5) + 31u - __clz(xm);
+    else
+        lo = run_start(bits, j);
+    if (above)
+        hi = (w << 5) + (unsigned)__ffs(above) - 1u;
+    else if (xp)
+        hi = ((w + 1u) << 5) + (unsigned)__ffs(xp) - 1u;
+    else
+        hi = run_end(bits, j, n);
+    hi = min(hi, n);
+}
+
+// Members of the run [lo, hi) below v: up to 8 with independent loads, then
+// one at a time.
+__device__ __forceinline__ unsigned rank_in_run(const unsigned *s_o, unsigned lo, unsigned hi, unsigned v)
+{
+    unsigned r = 0;
+#pragma unroll
+    for (unsigned q = 0; q < 8u; ++q) {
+        const unsigned i = lo + q;
+        if (i < hi) r += s_o[i] < v ? 1u : 0u;
+    }
+    for (unsigned i = lo + 8u; i < hi; ++i) r += s_o[i] < v ? 1u : 0u;
+    return r;
+}
+
+// A hint that brings [p, p + count) of a 32-bit array into L2 ahead of its
+// reads (one bulk prefetch; the range is shrunk to 16-byte boundaries inside
+// it, so no byte outside the array is named).
+__device__ __forceinline__ void l2_prefetch_u32(const unsigned *p, unsigned count)
+{
+    const unsigned long long b = (unsigned long long)p;
+    const unsigned long long lo = (b + 15ull) & ~15ull, hi = (b + 4ull * count) & ~15ull;
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 // One block per group of buckets, in passes over the group's pairs: count
 // them per cell (shared atomics), scan the counts into the cells' offsets
 // (written out as G), then place the pairs cell by cell in shared memory
 // (atomics on per-cell cursors hand out slots inside a cell in no fixed
 // order) and write each pair to its cell's offset plus its rank among the
 // cell's pairs by object id: the order a stable sort of object-order pairs
-// leaves them in.  A group of more than LOCAL_CAP pairs is placed in chunks
-// of whole cells (each chunk gathers its pairs in one more pass over the
-// group).  A group with a cell of more than LOCAL_RUN_MAX pairs is left
-// alone and flagged ERR_LOCAL_FALLBACK: the host then places the whole build
-// by radix passes over every key bit and range extraction instead.
+// leaves them in.  While a group runs, the block's next group's keys and
+// values are prefetched into L2.  A group of more than LOCAL_CAP pairs is
+// placed in chunks of whole cells (each chunk gathers its pairs in one more
+// pass over the group).  A group with a cell of more than LOCAL_RUN_MAX pairs
+// is left alone and flagged ERR_LOCAL_FALLBACK: the host then places the
+// whole build by radix passes over every key bit and range extraction instead.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, LOCAL_MIN_BLOCKS) local_sort_kernel(LocalArgs a)
 {
     constexpr int HN = 1 << LOCAL_LMAX;
+    constexpr int PER = HN / BLOCK;   // cells per thread in the scan
+    static_assert(HN % BLOCK == 0 && PER >= 1, "cells per thread");
     constexpr unsigned Q = (unsigned)LOCAL_CAP - LOCAL_RUN_MAX;   // chunk k: cells with offsets in [k Q, (k + 1) Q)
+    constexpr unsigned NBW = (unsigned)LOCAL_CAP / 32u;
     extern __shared__ __align__(16) unsigned smem[];
     unsigned *h = smem;                 // [HN + 1] per-cell counts, then offsets
     unsigned *hc = h + HN + 1;          // [HN] per-cell cursors of the current chunk
     unsigned *s_o = hc + HN;            // [LOCAL_CAP] the chunk's values, by cell
-    __shared__ unsigned s_bits[LOCAL_CAP / 32];   // one bit per position of s_o: a cell's run starts
+    __shared__ unsigned s_bits[NBW];    // one bit per position of s_o: a cell's run starts
     __shared__ unsigned s_tmp[BLOCK / 32];
-    __shared__ unsigned s_end, s_flag, s_clo, s_chi;
+    __shared__ unsigned s_end, s_clo, s_chi;
     const int tid = threadIdx.x;
     const unsigned ngroups = min(ld_relaxed_u32(&a.ctl->tickets[2]), a.max_groups);
     const unsigned bmax = (1u << LOCAL_LMAX) >> a.lbits;
+    // the pairs of group gg lie in [starts[b0], starts[min(b0 + bmax, nbuckets)])
+    auto prefetch = [&](unsigned gg) {
+        if (gg >= ngroups) return;
+        const unsigned b0 = a.groups[gg], e = min(b0 + bmax, a.nbuckets);
+        const unsigned s0 = a.starts[b0], s1 = a.starts[e];
+        if (s1 > s0) {
+            l2_prefetch_u32(a.keys + s0, s1 - s0);
+            l2_prefetch_u32(a.vals + s0, s1 - s0);
+        }
+    };
+    if (tid == 0) prefetch(blockIdx.x);
     // blocks take groups in turn: a fixed grid, no block without a group
     for (unsigned g = blockIdx.x; g < ngroups; g += gridDim.x) {
     __syncthreads();   // the previous group's last reads of shared memory are done
+    if (tid == 0) prefetch(g + gridDim.x);
     const unsigned b0 = a.groups[g];
     // the group's end: the next bucket that opens a group, at most bmax on
-    if (tid == 0) {
-        s_end = min(b0 + bmax, a.nbuckets);
-        s_flag = 0u;
+    unsigned b1 = min(b0 + bmax, a.nbuckets);
+    if (bmax > 1u) {
+        if (tid == 0) s_end = b1;
+        __syncthreads();
+        for (unsigned b = b0 + 1u + tid; b < b1; b += BLOCK) {
+            const unsigned sn = b + 1u < a.nbuckets ? a.starts[b + 1u] : a.count;
+            if (opens_group(b, a.starts[b - 1u], a.starts[b], sn, a.group_pairs, bmax)) atomicMin(&s_end, b);
+        }
+        __syncthreads();
+        b1 = s_end;
     }
-    __syncthreads();
-    for (unsigned b = b0 + 1u + tid; b < min(b0 + bmax, a.nbuckets); b += BLOCK) {
-        const unsigned sn = b + 1u < a.nbuckets ? a.starts[b + 1u] : a.count;
-        if (opens_group(b, a.starts[b - 1u], a.starts[b], sn, a.group_pairs, bmax)) atomicMin(&s_end, b);
-    }
-    __syncthreads();
-    const unsigned b1 = s_end;
     const unsigned long long cbase64 = (unsigned long long)b0 << a.lbits;
     const unsigned cbase = (unsigned)cbase64;
     const unsigned nh = (b1 - b0) << a.lbits;   // cells of the whole buckets, <= HN
@@ -1641,11 +1719,14 @@ __global__ void __launch_bounds__(BLOCK, LOCAL_MIN_BLOCKS) local_sort_kernel(Loc
     }
     const unsigned *keys = a.keys + s, *vals = a.vals + s;
     unsigned *refs = a.refs + s;
+    const bool one_chunk = m <= (unsigned)LOCAL_CAP;
     bool bad = false;
     // count the pairs per cell.  The loops over the group's pairs take U
     // pairs per thread at a time, every load issued before any is used.
     constexpr int U = 8;
-    for (unsigned c = tid; c < nh; c += BLOCK) h[c] = 0u;
+    for (unsigned c = tid; c < (unsigned)HN; c += BLOCK) h[c] = 0u;
+    if (one_chunk)
+        for (unsigned w = tid; w < NBW; w += BLOCK) s_bits[w] = 0u;
     __syncthreads();
     for (unsigned j0 = tid; j0 < m; j0 += U * BLOCK) {
         unsigned kk[U];
@@ -1661,19 +1742,66 @@ __global__ void __launch_bounds__(BLOCK, LOCAL_MIN_BLOCKS) local_sort_kernel(Loc
         }
     }
     __syncthreads();
-    bool long_run = false;
-    for (unsigned c = tid; c < nc; c += BLOCK) long_run |= h[c] > LOCAL_RUN_MAX;
-    if (long_run) s_flag = 1u;
-    scan_counts<BLOCK>(h, nh, s_tmp);
-    if (s_flag) {
-        if (tid == 0) atomicOr(&a.ctl->err, ERR_LOCAL_FALLBACK);
-        continue;
+    // scan the counts: thread t owns cells [t PER, (t + 1) PER); a cell
+    // of more than LOCAL_RUN_MAX pairs sends the build to the fallback.
+    // With one chunk the same pass also sets the placement cursors, marks
+    // each non-empty cell's run start and writes G.
+    {
+        const unsigned c0 = (unsigned)tid * PER;
+        unsigned cnt[PER];
+        if constexpr (PER == 4) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(h + c0);
+            cnt[0] = q.x; cnt[1] = q.y; cnt[2] = q.z; cnt[3] = q.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < PER; ++i) cnt[i] = h[c0 + i];
+        }
+        unsigned sum = 0;
+        bool long_run = false;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            sum += cnt[i];
+            long_run |= cnt[i] > (unsigned)LOCAL_RUN_MAX;
+        }
+        unsigned tot;
+        unsigned ex = block_excl_sum<BLOCK>(sum, s_tmp, &tot);
+        unsigned off[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            off[i] = ex;
+            ex += cnt[i];
+        }
+        if constexpr (PER == 4) {
+            *reinterpret_cast<uint4 *>(h + c0) = make_uint4(off[0], off[1], off[2], off[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < PER; ++i) h[c0 + i] = off[i];
+        }
+        if (tid == 0) h[HN] = tot;
+        if (one_chunk) {
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                hc[c0 + i] = off[i];
+                if (cnt[i]) atomicOr(&s_bits[off[i] >> 5], 1u << (off[i] & 31u));
+            }
+        }
+        unsigned *gp = a.G + cbase64 + c0;
+        if (PER == 4 && c0 + 4u <= nc && ((unsigned long long)gp & 15ull) == 0ull) {
+            *reinterpret_cast<uint4 *>(gp) = make_uint4(s + off[0], s + off[1 % PER], s + off[2 % PER], s + off[3 % PER]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < PER; ++i)
+                if (c0 + i < nc) gp[i] = s + off[i];
+        }
+        if (__syncthreads_or(long_run)) {
+            if (tid == 0) atomicOr(&a.ctl->err, ERR_LOCAL_FALLBACK);
+            continue;
+        }
     }
-    for (unsigned c = tid; c < nc; c += BLOCK) a.G[cbase64 + c] = s + h[c];
-    const unsigned nchunks = m > (unsigned)LOCAL_CAP ? (m + Q - 1u) / Q : 1u;
+    const unsigned nchunks = one_chunk ? 1u : (m + Q - 1u) / Q;
     for (unsigned k = 0; k < nchunks; ++k) {
         unsigned clo = 0, chi = nc;
-        if (nchunks > 1u) {   // the chunk's cells: binary searches over the offsets
+        if (!one_chunk) {   // the chunk's cells: binary searches over the offsets
             if (tid == 0) {
                 unsigned lo = 0, hi = nc;
                 while (lo < hi) {
@@ -1692,13 +1820,15 @@ __global__ void __launch_bounds__(BLOCK, LOCAL_MIN_BLOCKS) local_sort_kernel(Loc
             clo = s_clo;
             chi = s_chi;
         }
-        const unsigned base = h[clo], cm = h[chi] - base;   // the chunk's pairs: [base, base + cm)
-        for (unsigned w = tid; w < (cm + 31u) / 32u; w += BLOCK) s_bits[w] = 0u;
-        for (unsigned c = clo + tid; c < chi; c += BLOCK) hc[c] = h[c] - base;
-        __syncthreads();
-        for (unsigned c = clo + tid; c < chi; c += BLOCK) {
-            const unsigned p = h[c] - base;   // not hc[c]: placement below moves the cursors
-            if (h[c + 1] > h[c]) atomicOr(&s_bits[p >> 5], 1u << (p & 31u));
+        const unsigned base = h[clo], cm = (one_chunk ? m : h[chi]) - base;   // the chunk's pairs: [base, base + cm)
+        if (!one_chunk) {
+            for (unsigned w = tid; w < (cm + 31u) / 32u; w += BLOCK) s_bits[w] = 0u;
+            for (unsigned c = clo + tid; c < chi; c += BLOCK) hc[c] = h[c] - base;
+            __syncthreads();
+            for (unsigned c = clo + tid; c < chi; c += BLOCK) {
+                const unsigned p = h[c] - base;   // not hc[c]: placement below moves the cursors
+                if (h[c + 1] > h[c]) atomicOr(&s_bits[p >> 5], 1u << (p & 31u));
+            }
         }
         // place the chunk's pairs by cell (slots inside a cell in no fixed order)
         for (unsigned j0 = tid; j0 < m; j0 += U * BLOCK) {
@@ -1715,12 +1845,12 @@ __global__ void __launch_bounds__(BLOCK, LOCAL_MIN_BLOCKS) local_sort_kernel(Loc
         }
         __syncthreads();
         // each pair to its cell's start plus its rank by object id inside the cell
+        const unsigned nw = (cm + 31u) >> 5;
         for (unsigned j = tid; j < cm; j += BLOCK) {
             const unsigned v = s_o[j];
-            const unsigned lo = run_start(s_bits, j), hi = run_end(s_bits, j, cm);
-            unsigned r = 0;
-            for (unsigned i = lo; i < hi; ++i) r += s_o[i] < v ? 1u : 0u;
-            __stcs(refs + base + lo + r, v);
+            unsigned lo, hi;
+            run_bounds(s_bits, j, cm, nw, lo, hi);
+            __stcs(refs + base + lo + rank_in_run(s_o, lo, hi, v), v);
         }
         __syncthreads();
     }
@@ -1971,9 +2101,10 @@ static cudaError_t launch_down_b(const DownArgs &a, int rbits, int in, unsigned 
 {
 #define GG_DOWN(RB)                                                                                     \
     case RB:                                                                                            \
-        return in == IN_GEN    ? launch_down_t<RB, IN_GEN, BLOCK>(a, ntiles, gtiles, s)                 \
-               : in == IN_PAIR ? launch_down_t<RB, IN_PAIR, BLOCK>(a, ntiles, gtiles, s)                \
-                               : launch_down_t<RB, IN_PAIR, BLOCK, false>(a, ntiles, gtiles, s);
+        return in == IN_GEN         ? launch_down_t<RB, IN_GEN, BLOCK>(a, ntiles, gtiles, s)            \
+               : in == IN_PAIR      ? launch_down_t<RB, IN_PAIR, BLOCK>(a, ntiles, gtiles, s)           \
+               : in == IN_PAIR_KEEP ? launch_down_t<RB, IN_PAIR_KEEP, BLOCK>(a, ntiles, gtiles, s)      \
+                                    : launch_down_t<RB, IN_PAIR, BLOCK, false>(a, ntiles, gtiles, s);
     switch (rbits) {
         GG_DOWN(8)
         GG_DOWN(9)

@@ -141,7 +141,11 @@ struct UpArgs {
 // Downsweep of one pass: rank and scatter of each tile.  IN_PAIR_ANY reads
 // stored pairs like IN_PAIR but may rank equal digits of a warp out of
 // element order (the hybrid placement's first pass; see downsweep_kernel).
-enum { IN_GEN = 0, IN_PAIR = 1, IN_PAIR_ANY = 2 };
+// IN_PAIR_KEEP needs equal digits to keep only the order of key bits
+// [keep_lo, shift) (the hybrid placement's later passes: the order inside a
+// bucket is restored by the placement): a tile whose elements all share
+// those bits ranks like IN_PAIR_ANY, any other tile like IN_PAIR.
+enum { IN_GEN = 0, IN_PAIR = 1, IN_PAIR_ANY = 2, IN_PAIR_KEEP = 3 };
 
 struct DownArgs {
     const unsigned *keys_in;        // IN_PAIR
@@ -154,6 +158,7 @@ struct DownArgs {
     unsigned *vals_out;
     unsigned count;
     int shift, bits;
+    int keep_lo;                    // IN_PAIR_KEEP: lowest key bit whose order equal digits keep
     const unsigned *dbase;          // [2^bits] digit starts of this pass
     const unsigned *gpref;          // from the upsweep
     const unsigned short *intra;    // from the upsweep

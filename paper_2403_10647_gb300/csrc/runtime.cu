@@ -60,12 +60,13 @@ struct Scratch {
 
 enum KernelId {
     K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_LOCALIZE,
-    K_PER_OBJECT, K_CULL, K_BSPLIT, K_LOCAL, K_DOWN_ANY, K_PLAN, K_NUM
+    K_PER_OBJECT, K_CULL, K_BSPLIT, K_LOCAL, K_DOWN_ANY, K_PLAN, K_DOWN_KEEP, K_NUM
 };
 const char *const kKernelNames[K_NUM] = {"bounds",  "count_scan",    "tile_search",   "emit",
                                          "upsweep_gen", "downsweep_gen", "upsweep", "downsweep",
                                          "extract_split", "extract",   "localize", "make_pairs_per_object",
-                                         "cull_emit", "bucket_split", "local_sort", "downsweep_first", "plan"};
+                                         "cull_emit", "bucket_split", "local_sort", "downsweep_first", "plan",
+                                         "downsweep_keep"};
 
 struct PendingTiming {
     int kid;
@@ -379,8 +380,9 @@ unsigned pair_tiles(int64_t count) { return (unsigned)((count + gg::PAIR_TILE - 
 // it reads keys_in/vals_in.  The last pass writes keys_last / vals_last;
 // pass outputs alternate between those and one scratch pair of arrays so
 // the last lands there.  first_any: the first pass need not keep equal
-// digits in input order (the hybrid placement restores the order inside
-// each cell itself).
+// digits in input order, and the later ones need keep only the order of the
+// key bits below their digit down to the first pass's lowest bit (the hybrid
+// placement restores the order inside each bucket itself).
 int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const ObjRec *recs, int64_t nobj,
                const unsigned *tile_obj, unsigned res_x, unsigned res_y, const gg::MeshTab &mt,
                const unsigned *keys_in, const unsigned *vals_in, unsigned *keys_last, unsigned *vals_last,
@@ -468,8 +470,13 @@ int sort_pairs(grid_ctx *c, const SortCfg &sc, unsigned count, bool gen, const O
         a.gpref = (const unsigned *)c->gpref.ptr;
         a.intra = (const unsigned short *)c->intra.ptr;
         a.ctl = c->d_ctl;
-        const int in = gen_down ? gg::IN_GEN : (first && first_any ? gg::IN_PAIR_ANY : gg::IN_PAIR);
-        KernelScope ks(c, gen_down ? K_DOWN_GEN : (in == gg::IN_PAIR_ANY ? K_DOWN_ANY : K_DOWN),
+        const int in = gen_down ? gg::IN_GEN
+                       : first_any ? (first ? gg::IN_PAIR_ANY : gg::IN_PAIR_KEEP)
+                                   : gg::IN_PAIR;
+        a.keep_lo = sc.shift[0];
+        KernelScope ks(c, gen_down ? K_DOWN_GEN
+                          : in == gg::IN_PAIR_ANY ? K_DOWN_ANY
+                          : in == gg::IN_PAIR_KEEP ? K_DOWN_KEEP : K_DOWN,
                        gen_down ? 16.0 * nobj + 8.0 * count : 16.0 * count);
         GG_CUDA(gg::launch_downsweep(a, sc.rb[p], in, ntiles, gtiles, c->shape,
                                      c->stream));
