@@ -346,7 +346,7 @@ __device__ __forceinline__ unsigned long long warp_lookback64(unsigned long long
 }
 
 template <int BLOCK, int ITEMS>
-__global__ void __launch_bounds__(BLOCK) count_scan_kernel(CountArgs a)
+__global__ void __launch_bounds__(BLOCK, COUNT_MIN_BLOCKS) count_scan_kernel(CountArgs a)
 {
     constexpr int T = BLOCK * ITEMS;
     __shared__ unsigned long long s_pref[T];

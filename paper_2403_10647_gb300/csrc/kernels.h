@@ -25,8 +25,18 @@ namespace gg {
 #ifndef GG_GEN_MIN_BLOCKS
 #define GG_GEN_MIN_BLOCKS 6
 #endif
-constexpr int COUNT_BLOCK = 256;
-constexpr int COUNT_TILE = 2048;
+#ifndef GG_COUNT_BLOCK
+#define GG_COUNT_BLOCK 256
+#endif
+#ifndef GG_COUNT_TILE
+#define GG_COUNT_TILE 2048
+#endif
+#ifndef GG_COUNT_MIN_BLOCKS
+#define GG_COUNT_MIN_BLOCKS 6
+#endif
+constexpr int COUNT_BLOCK = GG_COUNT_BLOCK;
+constexpr int COUNT_TILE = GG_COUNT_TILE;
+constexpr int COUNT_MIN_BLOCKS = GG_COUNT_MIN_BLOCKS;   // resident count/scan blocks per SM compiled for
 constexpr int PAIR_BLOCK = GG_PAIR_BLOCK;
 constexpr int PAIR_TILE = GG_PAIR_BLOCK * GG_PAIR_ITEMS;
 constexpr int PASS_MIN_BLOCKS = GG_PASS_MIN_BLOCKS;
