@@ -17,7 +17,7 @@ namespace gg {
 #define GG_PAIR_ITEMS 12
 #endif
 #ifndef GG_PASS_MIN_BLOCKS
-#define GG_PASS_MIN_BLOCKS 4
+#define GG_PASS_MIN_BLOCKS 5
 #endif
 #ifndef GG_GROUP_TILES
 #define GG_GROUP_TILES 16
