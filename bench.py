@@ -159,13 +159,18 @@ def peaks():
 
 
 def kernels_digest() -> str:
-    """First 16 hex digits of the sha256 of csrc/kernels.cu's code with its
-    comments and whitespace removed: a comment edit keeps the committed
-    profiles valid, any code change does not."""
+    """First 16 hex digits of the sha256 of the kernels' code (csrc/kernels.cu,
+    kernels.h and device.cuh, in that order) with comments and whitespace
+    removed: a comment edit keeps the committed profiles valid, any code
+    change does not."""
     import hashlib
     import re
-    with open(os.path.join(ROOT, "paper_2403_10647_gb300", "csrc", "kernels.cu")) as f:
-        src = f.read()
+    src = ""
+    for name in ("kernels.cu", "kernels.h", "device.cuh"):
+        path = os.path.join(ROOT, "paper_2403_10647_gb300", "csrc", name)
+        if os.path.exists(path):
+            with open(path) as f:
+                src += f.read()
     src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
     src = re.sub(r"//[^\n]*", " ", src)
     src = re.sub(r"\s+", "", src)

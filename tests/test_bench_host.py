@@ -37,7 +37,13 @@ def test_digest_ignores_comments_and_whitespace(tmp_path, monkeypatch):
     assert bench.kernels_digest() == d0
     with open(p, "w") as f:
         f.write("int f(int a) {\n    return a + 2;\n}\n")
-    assert bench.kernels_digest() != d0
+    d1 = bench.kernels_digest()
+    assert d1 != d0
+    # a launch-shape constant in the kernels' header changes the code too
+    h = os.path.join(bench.ROOT, "paper_2403_10647_gb300", "csrc", "kernels.h")
+    with open(h, "w") as f:
+        f.write("#define BLOCKS 5\n")
+    assert bench.kernels_digest() != d1
 
 
 def test_traffic_lookup_needs_the_current_digest(tmp_path, monkeypatch):
