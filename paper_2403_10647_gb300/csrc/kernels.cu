@@ -940,14 +940,19 @@ __global__ void __launch_bounds__(BLOCK, SRC == SRC_GEN ? gen_min_blocks<BLOCK>(
     if (SRC == SRC_GEN) zero_marks<BLOCK, ITEMS>(s_mark);
     __syncthreads();
 
-    // a tile's keys, 16 bytes per load where the whole run is in range
+    // a tile's keys, 16 bytes per load where the whole run is in range and
+    // the array is 16-byte aligned (a batch's later sort segments start
+    // anywhere in the output arrays)
+    const bool kvec = (reinterpret_cast<unsigned long long>(a.keys_in) & 15ull) == 0ull;
+    const bool gvec = (reinterpret_cast<unsigned long long>(a.gen_keys) & 15ull) == 0ull &&
+                      (reinterpret_cast<unsigned long long>(a.gen_vals) & 15ull) == 0ull;
     auto load_keys = [&](unsigned t, unsigned (&k)[ITEMS]) {
         const unsigned j0 = t * (unsigned)T;
         const unsigned cnt = min((unsigned)T, a.count - j0);
 #pragma unroll
         for (int i = 0; i < ITEMS; i += 4) {
             const unsigned e = tid * ITEMS + i;
-            if (e + 3 < cnt) {
+            if (kvec && e + 3 < cnt) {
                 const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(a.keys_in + j0 + e));
                 k[i] = v.x;
                 k[i + 1] = v.y;
@@ -976,7 +981,7 @@ __global__ void __launch_bounds__(BLOCK, SRC == SRC_GEN ? gen_min_blocks<BLOCK>(
 #pragma unroll
                 for (int i = 0; i < ITEMS; i += 4) {
                     const unsigned e = tid * ITEMS + i;
-                    if (e + 3 < cnt) {
+                    if (gvec && e + 3 < cnt) {
                         __stcg(reinterpret_cast<uint4 *>(a.gen_keys + j0 + e),
                                make_uint4(keys[i], keys[i + 1], keys[i + 2], keys[i + 3]));
                         __stcg(reinterpret_cast<uint4 *>(a.gen_vals + j0 + e),
@@ -1953,6 +1958,25 @@ __global__ void __launch_bounds__(256) localize_kernel(const unsigned *__restric
     out[q] = __ldg(G + (q - lo)) - __ldg(pair_base + lo);
 }
 
+// A batch sorted in segments: each object's pair offset made relative to its
+// segment's first pair (segment s holds objects from seg_obj0[s]).
+__global__ void __launch_bounds__(256) rebase_recs_kernel(ObjRec *__restrict__ recs, long long n,
+                                                          const long long *__restrict__ seg_obj0,
+                                                          const unsigned *__restrict__ seg_p0, int nseg)
+{
+    const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    int lo = 0, hi = nseg - 1;   // largest s with seg_obj0[s] <= o
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(seg_obj0 + mid) <= o)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    recs[o].start -= __ldg(seg_p0 + lo);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -1981,6 +2005,14 @@ cudaError_t launch_localize(const unsigned *G, const long long *cells_off, const
 {
     if (total <= 0) return cudaSuccess;
     localize_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(G, cells_off, pair_base, nm, total, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebase_recs(ObjRec *recs, long long n, const long long *seg_obj0, const unsigned *seg_p0, int nseg,
+                               cudaStream_t s)
+{
+    if (n <= 0 || nseg < 1) return cudaSuccess;
+    rebase_recs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(recs, n, seg_obj0, seg_p0, nseg);
     return cudaGetLastError();
 }
 

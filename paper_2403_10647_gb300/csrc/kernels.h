@@ -208,6 +208,10 @@ cudaError_t launch_bounds(const float *verts, long long nverts, const int *tris,
 cudaError_t launch_bounds_batched(const MeshTab &mt, long long ntot, unsigned *bstate, Ctl *ctl, cudaStream_t s);
 // Batched: out[q] = G[q - m] - pair_base[m] for q in mesh m's slice
 // [cells_off[m], cells_off[m + 1]) of the per-mesh cell arrays.
+// Batched builds sorted in segments: recs[o].start -= seg_p0[s] for the
+// segment s holding object o (the last s with seg_obj0[s] <= o).
+cudaError_t launch_rebase_recs(ObjRec *recs, long long n, const long long *seg_obj0, const unsigned *seg_p0, int nseg,
+                               cudaStream_t s);
 cudaError_t launch_localize(const unsigned *G, const long long *cells_off, const unsigned *pair_base, int nm,
                             long long total, unsigned *out, cudaStream_t s);
 cudaError_t launch_count_scan(const CountArgs &a, cudaStream_t s);

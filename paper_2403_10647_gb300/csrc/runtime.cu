@@ -60,13 +60,13 @@ struct Scratch {
 
 enum KernelId {
     K_BOUNDS, K_COUNT, K_TILES, K_EMIT, K_UP_GEN, K_DOWN_GEN, K_UP, K_DOWN, K_SPLIT, K_EXTRACT, K_LOCALIZE,
-    K_PER_OBJECT, K_CULL, K_BSPLIT, K_LOCAL, K_DOWN_ANY, K_PLAN, K_DOWN_KEEP, K_NUM
+    K_PER_OBJECT, K_CULL, K_BSPLIT, K_LOCAL, K_DOWN_ANY, K_PLAN, K_DOWN_KEEP, K_REBASE, K_NUM
 };
 const char *const kKernelNames[K_NUM] = {"bounds",  "count_scan",    "tile_search",   "emit",
                                          "upsweep_gen", "downsweep_gen", "upsweep", "downsweep",
                                          "extract_split", "extract",   "localize", "make_pairs_per_object",
                                          "cull_emit", "bucket_split", "local_sort", "downsweep_first", "plan",
-                                         "downsweep_keep"};
+                                         "downsweep_keep", "rebase"};
 
 struct PendingTiming {
     int kid;
@@ -101,6 +101,7 @@ struct grid_ctx {
                                              // starts, bucket groups
     Scratch in_verts, in_tris, out_cells, out_refs;  // host-buffer builds
     Scratch b_desc, b_base, b_state, b_pairbase, b_cellsoff, b_G;   // batched builds
+    Scratch b_seg;                  // batched builds sorted in segments: the segments' tables
     Scratch pairs_C, pairs_O;    // object-order pairs of the unfused pair_gen modes and of culling
     void *h_stage = nullptr;     // pinned host tables of batched builds (grow-only)
     size_t h_stage_bytes = 0;
@@ -1114,7 +1115,7 @@ void grid_ctx_destroy(grid_ctx *c)
                           &c->vals_sorted, &c->bstarts, &c->bgroups,
                           &c->vals[0], &c->intra, &c->gpref, &c->gstatus, &c->in_verts, &c->in_tris,
                           &c->out_cells, &c->out_refs, &c->b_desc, &c->b_base, &c->b_state, &c->b_pairbase,
-                          &c->b_cellsoff, &c->b_G, &c->pairs_C, &c->pairs_O, &c->cstatus};
+                          &c->b_cellsoff, &c->b_G, &c->b_seg, &c->pairs_C, &c->pairs_O, &c->cstatus};
         for (Scratch *s : all) release(c, *s);
         if (c->stream) cudaStreamSynchronize(c->stream);
         resolve_timings(c);
@@ -1524,6 +1525,141 @@ int grid_build_host(grid_ctx *c, const float *h_verts, int64_t nverts, const int
     return rc;
 }
 
+// ---- batches sorted in segments ----------------------------------------------
+//
+// One sort over a whole batch keys its pairs by the batch's global cell id,
+// which can need a radix pass more than any of its meshes alone (64 meshes of
+// up to 7.7M cells: 27-bit keys, 4 passes of 8-bit digits, against 23 bits
+// and 3 passes for the largest mesh). The batch's pairs are generated mesh
+// after mesh, so consecutive meshes whose cells together fit the largest
+// mesh's pass count can be sorted, extracted and cut into their cells arrays
+// as one segment each, with keys counted from the segment's first cell.
+
+int key_bits_of(long long ncells)
+{
+    int b = 0;
+    for (unsigned long long v = ncells > 1 ? (unsigned long long)(ncells - 1) : 0ull; v; v >>= 1) ++b;
+    return b;
+}
+
+// The first mesh of every segment, then nm; false when one sort over the
+// whole batch takes no more radix passes than its largest mesh.
+bool sort_segments(const grid_ctx *c, const grid_info *infos, int nm, long long ncells_all, std::vector<int> &segs)
+{
+    int kmax = 0;
+    for (int m = 0; m < nm; ++m) kmax = std::max(kmax, key_bits_of(infos[m].ncells));
+    const int pmax = std::max(sort_cfg(kmax, c->rbits_max).passes, 1);
+    if (sort_cfg(key_bits_of(ncells_all), c->rbits_max).passes <= pmax) return false;
+    const long long cap = 1ll << std::min(pmax * c->rbits_max, 31);   // cells pmax passes sort
+    segs.assign(1, 0);
+    long long acc = 0;
+    for (int m = 0; m < nm; ++m) {
+        if (acc > 0 && acc + infos[m].ncells > cap) {
+            segs.push_back(m);
+            acc = 0;
+        }
+        acc += infos[m].ncells;
+    }
+    segs.push_back(nm);
+    return segs.size() > 2;
+}
+
+// Sort, range extraction and the cells arrays of a batch, segment by segment
+// (segs from sort_segments). desc, obj_base, pair_base (nm + 1 entries, the
+// last NO) and cells_off describe the whole batch as its count/scan left it;
+// recs hold global pair offsets on entry, segment-relative ones on return.
+int build_segments(grid_ctx *c, const std::vector<int> &segs, int nm, const gg::MeshDesc *desc,
+                   const long long *obj_base, const unsigned *pair_base, const long long *cells_off,
+                   const grid_info *infos, long long ntot, unsigned *refs, unsigned *cells)
+{
+    const int ns = (int)segs.size() - 1;
+    // per mesh a descriptor whose cell base counts from its segment's first
+    // cell, and its pair base from the segment's first pair; per segment its
+    // object bases and output cell offsets from its first mesh (m1 - m0 + 1
+    // entries at m0 + s), its first object and first pair
+    std::vector<gg::MeshDesc> d2(desc, desc + nm);
+    std::vector<long long> ob2(nm + ns), co2(nm + ns), sobj0(ns);
+    std::vector<unsigned> pb2(nm), sp0(ns);
+    for (int s = 0; s < ns; ++s) {
+        const int m0 = segs[s], m1 = segs[s + 1];
+        for (int m = m0; m < m1; ++m) {
+            d2[m].cell_base = desc[m].cell_base - desc[m0].cell_base;
+            pb2[m] = pair_base[m] - pair_base[m0];
+        }
+        for (int m = m0; m <= m1; ++m) {
+            ob2[m + s] = obj_base[m] - obj_base[m0];
+            co2[m + s] = cells_off[m] - cells_off[m0];
+        }
+        sobj0[s] = obj_base[m0];
+        sp0[s] = pair_base[m0];
+    }
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t o_d = 0, o_ob = o_d + al(sizeof(gg::MeshDesc) * nm), o_co = o_ob + al(8 * (size_t)(nm + ns)),
+                 o_so = o_co + al(8 * (size_t)(nm + ns)), o_pb = o_so + al(8 * (size_t)ns),
+                 o_sp = o_pb + al(4 * (size_t)nm), total = o_sp + al(4 * (size_t)ns);
+    GG_TRY(ensure(c, c->b_seg, total));
+    char *base = (char *)c->b_seg.ptr;
+    GG_CUDA(cudaMemcpyAsync(base + o_d, d2.data(), sizeof(gg::MeshDesc) * nm, cudaMemcpyHostToDevice, c->stream));
+    GG_CUDA(cudaMemcpyAsync(base + o_ob, ob2.data(), 8 * (size_t)(nm + ns), cudaMemcpyHostToDevice, c->stream));
+    GG_CUDA(cudaMemcpyAsync(base + o_co, co2.data(), 8 * (size_t)(nm + ns), cudaMemcpyHostToDevice, c->stream));
+    GG_CUDA(cudaMemcpyAsync(base + o_so, sobj0.data(), 8 * (size_t)ns, cudaMemcpyHostToDevice, c->stream));
+    GG_CUDA(cudaMemcpyAsync(base + o_pb, pb2.data(), 4 * (size_t)nm, cudaMemcpyHostToDevice, c->stream));
+    GG_CUDA(cudaMemcpyAsync(base + o_sp, sp0.data(), 4 * (size_t)ns, cudaMemcpyHostToDevice, c->stream));
+    const gg::MeshDesc *d_desc = (const gg::MeshDesc *)(base + o_d);
+    const long long *d_ob = (const long long *)(base + o_ob), *d_co = (const long long *)(base + o_co);
+    const unsigned *d_pb = (const unsigned *)(base + o_pb);
+    ObjRec *recs = (ObjRec *)c->recs.ptr;
+    {
+        KernelScope ks(c, K_REBASE, 8.0 * ntot);
+        GG_CUDA(gg::launch_rebase_recs(recs, ntot, (const long long *)(base + o_so), (const unsigned *)(base + o_sp),
+                                       ns, c->stream));
+    }
+    unsigned *G = (unsigned *)c->b_G.ptr;
+    for (int s = 0; s < ns; ++s) {
+        const int m0 = segs[s], m1 = segs[s + 1];
+        const long long obj0 = obj_base[m0], n_s = obj_base[m1] - obj0;
+        const unsigned P0 = pair_base[m0], count = pair_base[m1] - P0;
+        const long long ncells_s = (long long)desc[m1 - 1].cell_base + infos[m1 - 1].ncells - desc[m0].cell_base;
+        unsigned *Gs = G + desc[m0].cell_base;   // the segment's cells, its own pair offsets
+        const gg::MeshTab mt{d_desc + m0, d_ob + m0 + s, m1 - m0};
+        if (count > 0) {
+            const ObjRec *recs_s = recs + obj0;
+            const unsigned ntiles = pair_tiles(count);
+            GG_TRY(ensure(c, c->tile_obj, (size_t)(ntiles + 1) * sizeof(unsigned)));
+            unsigned *tile_obj = (unsigned *)c->tile_obj.ptr;
+            {
+                KernelScope ks(c, K_TILES, 4.0 * (ntiles + 1));
+                GG_CUDA(gg::launch_tile_search(recs_s, n_s, gg::PAIR_TILE, ntiles, tile_obj, c->stream));
+            }
+            GG_TRY(ensure(c, c->keys_sorted, (size_t)count * sizeof(unsigned)));
+            unsigned *keys_sorted = (unsigned *)c->keys_sorted.ptr;
+            const SortCfg sc = sort_cfg(key_bits_of(ncells_s), c->rbits_max);
+            if (sc.passes == 0) {
+                gg::EmitArgs ea{};
+                ea.recs = recs_s;
+                ea.tile_obj = tile_obj;
+                ea.mt = mt;
+                ea.count = count;
+                ea.C = keys_sorted;
+                ea.O = refs + P0;
+                KernelScope ks(c, K_EMIT, 16.0 * n_s + 8.0 * count);
+                GG_CUDA(gg::launch_emit(ea, c->stream));
+            } else {
+                GG_TRY(sort_pairs(c, sc, count, true, recs_s, n_s, tile_obj, 0, 0, mt, nullptr, nullptr, keys_sorted,
+                                  refs + P0));
+            }
+            GG_TRY(extract_ranges(c, keys_sorted, count, ncells_s, Gs));
+        } else {
+            GG_CUDA(cudaMemsetAsync(Gs, 0, (size_t)(ncells_s + 1) * sizeof(unsigned), c->stream));
+        }
+        // before the next segment's extraction overwrites this one's last entry
+        const long long nq = cells_off[m1] - cells_off[m0];
+        KernelScope ks(c, K_LOCALIZE, 8.0 * nq);
+        GG_CUDA(gg::launch_localize(Gs, d_co + m0 + s, d_pb + m0, m1 - m0, nq, cells + cells_off[m0], c->stream));
+    }
+    return read_ctl(c);   // the host tables above stay alive until the copies have run
+}
+
 int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, grid_buf *out_cells,
                        grid_buf *out_refs, grid_info *infos, int64_t *cells_offsets, int64_t *refs_offsets)
 {
@@ -1656,6 +1792,13 @@ int grid_build_batched(grid_ctx *c, const grid_mesh *meshes, int32_t nmeshes, gr
     rc = [&]() -> int {
         GG_TRY(ensure(c, c->b_G, (size_t)(ncells_all + 1) * sizeof(unsigned)));
         unsigned *G = (unsigned *)c->b_G.ptr;
+        std::vector<int> segs;
+        if (NO > 0 && !use_hybrid(c, (unsigned)NO, ncells_all) && sort_segments(c, infos, nm, ncells_all, segs)) {
+            GG_TRY(build_segments(c, segs, nm, desc, obj_base, pair_base, cells_off, infos, ntot, (unsigned *)pr,
+                                  (unsigned *)pc));
+            c->stage_busy = false;
+            return ctl_error(c->h_ctl->err);
+        }
         if (NO > 0) {
             const unsigned count = (unsigned)NO;
             const unsigned ntiles = pair_tiles(count);

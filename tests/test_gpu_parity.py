@@ -460,6 +460,42 @@ def test_batched_matches_oracle_and_plain(ctx):
             assert torch.equal(p.cells, g.cells) and torch.equal(p.refs, g.refs), s.name
 
 
+def test_batched_sort_segments_match_oracle_and_plain():
+    """A batch whose global cell ids need a radix pass more than any of its
+    meshes is sorted in segments of consecutive meshes (keys counted from
+    each segment's first cell): every mesh equals its own build and the
+    oracle, with empty meshes and single triangles between segments."""
+    import paper_2403_10647_gb300 as pg
+    g = np.random.Generator(np.random.Philox(4343))
+    batch = []
+    for k in range(6):
+        batch.append(scenes.uniform_soup(4_000 + 700 * k, seed=210 + k))
+        if k == 2:
+            batch.append(scenes.Scene("empty", np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), 4.0))
+        if k == 4:
+            batch.append(scenes.tiny_scene(g, 1))
+    batch.append(scenes.nonhomogeneous_soup(6_000, seed=220, extent=12.0))
+    lam = 8.0
+    c = pg.Context(0, radix_bits=8, local_bits=-1)
+    try:
+        args = [(dev(s.verts, torch.float32), dev(s.tris, torch.int32), lam) for s in batch]
+        c.profile(True)
+        grids = c.build_batched(args)
+        st = c.kernel_stats()
+        c.profile(False)
+        ncells = [int(gr.info.ncells) for gr in grids]
+        assert max(ncells) <= 1 << 16 < sum(ncells), ncells   # 2 passes each, 3 for the whole batch
+        assert "rebase" in st, st.keys()
+        for s, gr in zip(batch, grids):
+            o = oracle.build_grid(s.verts, s.tris, lam, method="alg1")
+            assert_grid_equal(gr, o, f"segmented batch {s.name}")
+            if s.n:
+                p = c.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), lam)
+                assert torch.equal(p.cells, gr.cells) and torch.equal(p.refs, gr.refs), s.name
+    finally:
+        c.close()
+
+
 def test_batched_signed_zero_bounds(ctx):
     """Per-mesh bounds of a batch report zero bounds as +0.0, as plain builds
     and the oracle do (bit patterns compared)."""
