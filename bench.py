@@ -68,8 +68,9 @@ def parse():
     ap.add_argument("--tile-shape", default="256x12", choices=["256x12", "384x8"],
                     help="block shape of the radix-sort kernels of the timed builds")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-threads", type=int, default=2,
-                    help="host threads issuing grid_build_host calls for the end-to-end number")
+    ap.add_argument("--e2e-threads", type=int, default=4,
+                    help="host threads issuing grid_build_host calls for the end-to-end number "
+                         "(4: enough calls in flight to keep both copy directions busy)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-build and serving measurements")
