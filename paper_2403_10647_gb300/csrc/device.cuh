@@ -15,6 +15,8 @@ constexpr unsigned ERR_OVERFLOW = 4u;   // a prefix sum passed INT32_MAX
 constexpr unsigned ERR_TIMEOUT = 8u;    // a bounded look-back wait gave up
 constexpr unsigned ERR_RANGE = 16u;     // a key outside [0, ncells) or out of order reached range
                                         // extraction, or a sort scatter fell outside the output
+constexpr unsigned ERR_TILE_REDO = 64u;        // not an error: count/scan could not record every pair
+                                               // tile's first object; the host runs tile_search
 constexpr unsigned ERR_LOCAL_FALLBACK = 32u;   // not an error: a group of buckets too large for the
                                                // per-bucket counting sort; the host places the build
                                                // by radix passes over every key bit instead

@@ -449,18 +449,37 @@ __global__ void __launch_bounds__(BLOCK, COUNT_MIN_BLOCKS) count_scan_kernel(Cou
     }
     __syncthreads();
     const unsigned long long excl = s_excl;
+    bool tile_redo = false;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const long long o = base + i * BLOCK + tid;
+        const int p = i * BLOCK + tid;
+        const long long o = base + p;
         if (o < a.n) {
-            const unsigned start = (unsigned)(excl + s_pref[i * BLOCK + tid]);
+            const unsigned start = (unsigned)(excl + s_pref[p]);
             a.recs[o].start = start;
             if (a.mt.md) {
                 const int m = mesh_of(a.mt, o);
                 if (__ldg(a.mt.obj_base + m) == o) a.pair_base[m] = start;
             }
+            if (a.tile_obj && excl + total <= 0x7FFFFFFFull) {
+                // the pair tiles whose first pair is one of this object's
+                // [start, end): tile_search's answer, recorded here
+                const unsigned end = (unsigned)(excl + (p + 1 < T ? s_pref[p + 1] : total));
+                const unsigned t0 = (start + (unsigned)PAIR_TILE - 1u) / (unsigned)PAIR_TILE;
+                const unsigned tl = (end - 1u) / (unsigned)PAIR_TILE + 1u;   // tiles t0 .. tl - 1 (end > start)
+                if (tl <= a.tile_cap && tl - t0 <= 64u) {
+                    for (unsigned t = t0; t < tl; ++t) a.tile_obj[t] = (unsigned)o;
+                } else if (tl > t0) {
+                    tile_redo = true;
+                }
+                if (o == a.n - 1) {   // the entry after the last tile
+                    const unsigned nt = (end + (unsigned)PAIR_TILE - 1u) / (unsigned)PAIR_TILE;
+                    if (nt < a.tile_cap) a.tile_obj[nt] = (unsigned)o; else tile_redo = true;
+                }
+            }
         }
     }
+    if (tile_redo) atomicOr(&a.ctl->err, ERR_TILE_REDO);
 }
 
 // ---------------------------------------------------------------------------

@@ -95,6 +95,9 @@ struct CountArgs {
     MeshTab mt;                     // batched: per-object mesh (verts, tris, plan)
     unsigned *pair_base;            // batched: [nm] out, pair offset of each mesh's first object
     bool device_plan;               // single mesh: take lo / scale / res from ctl->plan_* instead
+    unsigned *tile_obj;             // single mesh, optional: [tile_cap] the first object of every
+    unsigned tile_cap;              // PAIR_TILE-pair tile and, after the last tile, n - 1 (tile_search's
+                                    // result), or ERR_TILE_REDO when it did not fit
 };
 
 struct EmitArgs {

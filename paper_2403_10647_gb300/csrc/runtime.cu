@@ -261,7 +261,7 @@ void resolve_timings(grid_ctx *c)
 // Error bits raised by the kernels -> GRID_* code.
 int ctl_error(unsigned err)
 {
-    err &= ~gg::ERR_LOCAL_FALLBACK;   // a request to the host, handled where it can arise
+    err &= ~(gg::ERR_LOCAL_FALLBACK | gg::ERR_TILE_REDO);   // requests to the host, handled where they arise
     if (err & (gg::ERR_BADINDEX | gg::ERR_NONFINITE | gg::ERR_RANGE)) return GRID_EINVAL;
     if (err & gg::ERR_OVERFLOW) return GRID_EOVERFLOW;
     if (err & gg::ERR_TIMEOUT) return GRID_ETIMEOUT;
@@ -786,6 +786,10 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
     ca.status = (unsigned long long *)c->k2status.ptr;
     ca.ctl = c->d_ctl;
     ca.device_plan = true;
+    // the pair tiles' first objects come out of the count when the buffer
+    // kept from earlier builds holds them
+    ca.tile_obj = (unsigned *)c->tile_obj.ptr;
+    ca.tile_cap = (unsigned)std::min<size_t>(c->tile_obj.bytes / sizeof(unsigned), 0xFFFFFFFFull);
     auto count_scan = [&]() -> int {
         GG_CUDA(cudaMemsetAsync(c->k2status.ptr, 0, (size_t)ctiles * 8, c->stream));
         KernelScope ks(c, K_COUNT, 64.0 * n);
@@ -887,10 +891,12 @@ int build_core(grid_ctx *c, const float *verts, int64_t nverts, const int32_t *t
     const SortCfg sc = sort_cfg(I.key_bits, c->rbits_max);
     if (count > 0) {
         const unsigned ntiles = pair_tiles(count);
+        const bool tiles_done = ca.tile_obj && (size_t)ntiles + 1 <= ca.tile_cap &&
+                                !(c->h_ctl->err & gg::ERR_TILE_REDO);
         GG_TRY(ensure(c, c->tile_obj, (size_t)(ntiles + 1) * sizeof(unsigned)));
         const ObjRec *recs = (const ObjRec *)c->recs.ptr;
         unsigned *tile_obj = (unsigned *)c->tile_obj.ptr;
-        {
+        if (!tiles_done) {
             KernelScope ks(c, K_TILES, 4.0 * (ntiles + 1));
             GG_CUDA(gg::launch_tile_search(recs, n, gg::PAIR_TILE, ntiles, tile_obj, c->stream));
         }
