@@ -642,3 +642,41 @@ def test_device_plan_random_bounds_match_oracle(ctx):
         assert np.array_equal(np.array(gr.info.scale, np.float32).view(np.uint32), p.scale.view(np.uint32)), k
         o = oracle.build_grid(v, t, lam, method="counting")
         assert np.array_equal(host(gr.cells), o.G) and np.array_equal(host(gr.refs), o.refs), k
+
+
+def _giant_triangle_scene(n_small, seed):
+    """One triangle spanning the scene's whole box (so its pairs cover a few
+    hundred pair tiles), placed in the middle of the object order, among
+    small ones."""
+    g = np.random.Generator(np.random.Philox(seed))
+    c = g.random((n_small, 3)) * 10.0
+    v = np.concatenate([c, c + 0.02, c + [0.02, 0.0, 0.02]]).astype(np.float32)
+    tris = np.stack([np.arange(n_small), n_small + np.arange(n_small), 2 * n_small + np.arange(n_small)], 1)
+    big_v = np.array([[0.0, 0.0, 0.0], [10.0, 0.0, 10.0], [0.0, 10.0, 10.0]], np.float32)
+    v = np.concatenate([v, big_v])
+    big = np.arange(3 * n_small, 3 * n_small + 3)[None, :]
+    tris = np.concatenate([tris[: n_small // 2], big, tris[n_small // 2:]]).astype(np.int32)
+    return scenes.Scene("giant", v, tris, 16.0)
+
+
+def test_pair_tiles_across_builds_of_one_context():
+    """A context records the pair tiles' first objects during count/scan once
+    its tile buffer is large enough, and falls back to the search otherwise
+    (the first build, a larger build, an object over more than 64 tiles):
+    every build of a growing and shrinking sequence equals the oracle."""
+    import paper_2403_10647_gb300 as pg
+    seq = [scenes.uniform_soup(3_000, seed=601), scenes.uniform_soup(30_000, seed=602),
+           _giant_triangle_scene(20_000, seed=603), scenes.uniform_soup(3_000, seed=601),
+           scenes.nonhomogeneous_soup(40_000, seed=604, extent=20.0), _giant_triangle_scene(20_000, seed=603)]
+    c = pg.Context(0)
+    try:
+        for k, s in enumerate(seq):
+            o = oracle.build_grid(s.verts, s.tris, s.lam, method="counting")
+            for rep in range(2):   # the second build of a scene runs with the buffer the first sized
+                g = c.build(dev(s.verts, torch.float32), dev(s.tris, torch.int32), s.lam)
+                assert_grid_equal(g, o, f"build {k} ({s.name}) rep {rep}")
+        giant = seq[2]
+        o = oracle.build_grid(giant.verts, giant.tris, giant.lam, method="counting")
+        assert int(np.diff(o.G).max()) >= 1 and o.NO > 64 * 3072 + 20_000   # the giant object spans > 64 tiles
+    finally:
+        c.close()
