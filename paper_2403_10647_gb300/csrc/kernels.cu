@@ -1562,18 +1562,25 @@ __device__ __forceinline__ unsigned bucket_start(const LocalArgs &a, unsigned b)
     return lo;
 }
 
+// Each block searches the starts of its 256 buckets and of the two next to
+// them once, shares them in shared memory, and opens the groups.
 __global__ void __launch_bounds__(256) bucket_split_kernel(LocalArgs a)
 {
-    const unsigned b = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ unsigned s_st[256 + 2];   // starts of buckets b0 - 1 .. b0 + 256
+    const unsigned b0 = blockIdx.x * 256u, b = b0 + threadIdx.x;
+    if (b <= a.nbuckets) s_st[threadIdx.x + 1] = bucket_start(a, b);
+    if (threadIdx.x == 0) s_st[0] = b0 ? bucket_start(a, b0 - 1u) : 0u;
+    if (threadIdx.x == 255 && b + 1u <= a.nbuckets) s_st[257] = bucket_start(a, b + 1u);
+    __syncthreads();
     if (b > a.nbuckets) return;
-    const unsigned sb = bucket_start(a, b);
+    const unsigned sb = s_st[threadIdx.x + 1];
     a.starts[b] = sb;
     if (b == a.nbuckets) {
         a.G[a.ncells] = a.count;
         return;
     }
     const unsigned bmax = (1u << LOCAL_LMAX) >> a.lbits;
-    const unsigned sp = b ? bucket_start(a, b - 1u) : 0u, sn = bucket_start(a, b + 1u);
+    const unsigned sp = b ? s_st[threadIdx.x] : 0u, sn = s_st[threadIdx.x + 2];
     if (opens_group(b, sp, sb, sn, a.group_pairs, bmax)) {
         const unsigned g = atomicAdd(&a.ctl->tickets[2], 1u);
         if (g < a.max_groups)
