@@ -180,6 +180,7 @@ __device__ __forceinline__ void gen_blocked(const ObjRec *__restrict__ recs, uns
     const unsigned e0 = threadIdx.x * ITEMS;
     unsigned o = 0u, x = 0u, y = 0u, z = 0u, mx = 1u, my = 1u, lox = 0u, loy = 0u, loz = 0u;
     unsigned rx = res_x, ry = res_y, kbase = 0u, obase = 0u;
+    unsigned key = 0u, dy = 0u, dz = 0u;   // the current key and its steps to the next row and slab
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const unsigned e = e0 + i;
@@ -212,14 +213,21 @@ __device__ __forceinline__ void gen_blocked(const ObjRec *__restrict__ recs, uns
                 } else {
                     x = y = z = 0u;
                 }
+                key = kbase + (lox + x) + rx * ((loy + y) + ry * (loz + z));
+                dy = rx - (mx - 1u);                    // from a row's last cell to the next row's first
+                dz = rx * ry - (my - 1u) * rx - (mx - 1u);   // from a slab's last cell to the next slab's first
             } else if (++x == mx) {
                 x = 0u;
                 if (++y == my) {
                     y = 0u;
-                    ++z;
+                    key += dz;
+                } else {
+                    key += dy;
                 }
+            } else {
+                ++key;
             }
-            keys[i] = kbase + (lox + x) + rx * ((loy + y) + ry * (loz + z));
+            keys[i] = key;
             objs[i] = o - obase;
         }
     }
